@@ -1,0 +1,178 @@
+"""FP64 CPU oracle of the coupled LBM + WENO5 step (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library (``paper_2106_07694_gb300``) and never imports it.
+
+The arithmetic lives in ``lbm_wenoc_oracle.c`` (one routine per step a1..a9 of
+the method; see its header for the passages each follows).  This module only
+marshals numpy arrays.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ORC_PERIODIC_VERTICAL = 1
+ORC_FROZEN_VELOCITY = 2
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("gravity", ctypes.c_double),
+        ("density_contrast", ctypes.c_double),
+        ("settling_velocity", ctypes.c_double),
+        ("diffusivity", ctypes.c_double),
+        ("lf_alpha", ctypes.c_double),
+        ("u_cap", ctypes.c_double),
+        ("body_force", ctypes.c_double * 3),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_create.argtypes = [ctypes.POINTER(_Params)]
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_init.argtypes = [ctypes.c_void_p, dp, dp]
+        L.orc_init.restype = ctypes.c_int
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        L.orc_population_moments.argtypes = [ctypes.c_void_p, dp]
+        L.orc_deposit.argtypes = [ctypes.c_void_p]
+        L.orc_deposit.restype = ctypes.c_double
+        L.orc_total_mass.argtypes = [ctypes.c_void_p]
+        L.orc_total_mass.restype = ctypes.c_double
+        L.orc_alpha.argtypes = [ctypes.c_void_p]
+        L.orc_alpha.restype = ctypes.c_double
+        L.orc_steps.argtypes = [ctypes.c_void_p]
+        L.orc_steps.restype = ctypes.c_int64
+        L.orc_transport_rate.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        L.orc_weno5_left.argtypes = [dp, ctypes.c_double]
+        L.orc_weno5_left.restype = ctypes.c_double
+        L.orc_lattice.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_lattice.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def weno5_left(v, eps):
+    """One WENO5-JS face value from the five upwind-side values v[0..4] = h_{i-2..i+2}."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.shape == (5,)
+    return lib().orc_weno5_left(_dptr(v), float(eps))
+
+
+class OracleSim:
+    """A simulation held by the C oracle.
+
+    shape: (nx, ny) in 2D or (nx, ny, nz) in 3D; arrays are indexed [z][y][x]
+    (numpy shape (ny, nx) or (nz, ny, nx)); the vertical axis is the slowest one.
+    """
+
+    def __init__(self, shape, tau=0.6, gravity=1.0, density_contrast=0.0,
+                 settling_velocity=0.0, diffusivity=0.0, lf_alpha=0.0, u_cap=0.0,
+                 body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False):
+        dim = len(shape)
+        p = _Params()
+        p.dim = dim
+        p.nx, p.ny = int(shape[0]), int(shape[1])
+        p.nz = int(shape[2]) if dim == 3 else 1
+        p.tau, p.gravity, p.density_contrast = tau, gravity, density_contrast
+        p.settling_velocity, p.diffusivity = settling_velocity, diffusivity
+        p.lf_alpha, p.u_cap = lf_alpha, u_cap
+        for d in range(3):
+            p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
+        p.flags = (ORC_PERIODIC_VERTICAL if periodic_vertical else 0) | \
+                  (ORC_FROZEN_VELOCITY if frozen_velocity else 0)
+        self._p = p
+        self.dim = dim
+        self.grid = tuple(reversed([int(s) for s in shape]))  # numpy shape, vertical first
+        self.n = int(np.prod(self.grid))
+        h = lib().orc_create(ctypes.byref(p))
+        if not h:
+            raise ValueError("oracle rejected the parameters")
+        self._h = ctypes.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_destroy(h)
+            self._h = None
+
+    @property
+    def alpha(self):
+        return lib().orc_alpha(self._h)
+
+    def init(self, c0, u0=None):
+        c0 = np.ascontiguousarray(c0, dtype=np.float64).reshape(self.grid)
+        self._c0_keep = c0
+        up = None
+        if u0 is not None:
+            u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape((self.dim,) + self.grid)
+            self._u0_keep = u0
+            up = _dptr(u0)
+        rc = lib().orc_init(self._h, _dptr(c0), up)
+        if rc != 0:
+            raise RuntimeError(f"orc_init failed: {rc}")
+
+    def step(self, n=1):
+        return lib().orc_step(self._h, int(n))
+
+    def fields(self):
+        rho = np.empty(self.grid)
+        u = np.empty((self.dim,) + self.grid)
+        c = np.empty(self.grid)
+        lib().orc_fields(self._h, _dptr(rho), _dptr(u), _dptr(c))
+        return rho, u, c
+
+    def population_moments(self):
+        out = np.empty(4)
+        lib().orc_population_moments(self._h, _dptr(out))
+        return out
+
+    @property
+    def deposit(self):
+        return lib().orc_deposit(self._h)
+
+    @property
+    def total_mass(self):
+        return lib().orc_total_mass(self._h)
+
+    @property
+    def steps(self):
+        return lib().orc_steps(self._h)
+
+    def transport_rate(self, c, u):
+        """L(c) for a given c and transport velocity u (shape (dim,)+grid)."""
+        c = np.ascontiguousarray(c, dtype=np.float64).reshape(self.grid)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape((self.dim,) + self.grid)
+        L = np.empty(self.grid)
+        lib().orc_transport_rate(self._h, _dptr(c), _dptr(u), _dptr(L))
+        return L
+
+    def lattice(self):
+        ci = (ctypes.c_int * 57)()
+        wi = np.empty(19)
+        q = lib().orc_lattice(self._h, ci, _dptr(wi))
+        return np.array(ci[: 3 * q]).reshape(q, 3), wi[:q].copy()

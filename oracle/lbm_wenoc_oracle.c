@@ -1,0 +1,519 @@
+/*
+ * FP64 CPU oracle of the coupled lattice-Boltzmann + WENO5 time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what one step of the method computes.  Only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark load it.  It shares no
+ * code, table or header with the CUDA library and must never be called by it.
+ *
+ * Every routine follows the paper's statement of the method, step by step,
+ * in double precision, with plain loops over nodes (OpenMP only splits those
+ * loops; reductions are serial and in index order):
+ *
+ *   a1  moments   rho = sum f_i,  rho u = sum f_i c_i + F/2        (Sec. 2.3.1, Eqs. dens, mom_dens, LBE_Guo)
+ *   a2  BGK collision with the Guo (2002) source term              (Sec. 2.3.1, Eqs. LBE, LBE_Guo, tau)
+ *   a3  streaming with halfway bounce-back at floor and lid        (Sec. 2.3.1, no-slip walls of Sec. 2.2.1)
+ *   a4  global Lax-Friedrichs split  h+- = (w +- alpha) c / 2     (Supplement Eqs. S8, S17-S20 "upwind splitting")
+ *   a5  WENO5 (Jiang & Shu 1996) face reconstruction              (Supplement Eqs. S9-S16, order raised to 5)
+ *   a6  central diffusion flux  kappa (c_{i+1} - c_i)              (Supplement Eq. S4; Eq. ADS)
+ *   a7  conservative divergence of the face fluxes                 (Supplement Eq. S9; Eq. ADS)
+ *   a8  SSP-RK3 (Shu-Osher) with the velocity frozen at step n     (Supplement Eqs. S21-S23)
+ *   a9  deposit: settling flux through the floor, RK3 b-weights    (Sec. 4, deposited mass m_b)
+ *
+ * Readings of points the paper leaves open (garbled LBE right-hand side,
+ * WENO order, split, epsilon, wall fluxes, coupling order, initial state) are
+ * the ones listed in the design notes: fluid nodes sit at v = 0..N-1 on the
+ * vertical axis, walls at v = -1/2 and v = N-1/2; stencils that cross a wall
+ * read ghosts with c even-reflected (Neumann, Eq. neum1) and the fluid
+ * velocity odd-reflected (no-slip); the lid face carries no flux and the floor
+ * face carries the settling outflow -Vs c_0, which is tallied as deposit.
+ *
+ * Lattice units throughout (dx = dt = 1, c_s^2 = 1/3).  Vertical axis = y in
+ * 2D, z in 3D.  Node index = (z*ny + y)*nx + x.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PERIODIC_VERTICAL 1u /* vertical axis periodic too: no walls, no deposit */
+#define ORC_FROZEN_VELOCITY 2u   /* fluid not advanced; transport uses the velocity given at init */
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+#define ORC_EUNSTABLE -4
+
+typedef struct {
+  int32_t dim; /* 2 or 3 */
+  int32_t nx, ny, nz;
+  double tau;
+  double gravity;
+  double density_contrast;
+  double settling_velocity;
+  double diffusivity;
+  double lf_alpha; /* 0 selects settling_velocity + u_cap */
+  double u_cap;    /* 0 selects 0.1 */
+  double body_force[3];
+  uint32_t flags;
+} orc_params;
+
+typedef struct {
+  orc_params p;
+  int Q;
+  int ci[19][3];
+  double wi[19];
+  int opp[19];
+  int n[3];     /* extents along x, y, z (z = 1 in 2D) */
+  size_t nn;    /* number of nodes */
+  int vaxis;    /* index of the vertical axis */
+  double alpha; /* Lax-Friedrichs split speed */
+  double eps;   /* WENO epsilon = 1e-6 alpha^2 */
+  double *f;    /* populations, natural layout f[i*nn + node] */
+  double *fpost;
+  double *c;
+  double *u; /* dim*nn: velocity that transports c during the current step */
+  double *rho;
+  double *c1, *c2, *L, *flux;
+  double deposit;
+  int64_t steps;
+  int status;
+} orc_sim;
+
+/* ---- velocity sets (Kruger et al. 2017, the LBM text the paper cites) ---- */
+
+static void set_d2q9(orc_sim *s) {
+  /* rest, 4 axis neighbours (w = 1/9), 4 diagonals (w = 1/36) */
+  static const int c[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1},
+                              {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+  s->Q = 9;
+  for (int i = 0; i < 9; ++i) {
+    s->ci[i][0] = c[i][0];
+    s->ci[i][1] = c[i][1];
+    s->ci[i][2] = 0;
+    int len2 = c[i][0] * c[i][0] + c[i][1] * c[i][1];
+    s->wi[i] = len2 == 0 ? 4.0 / 9.0 : (len2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+}
+
+static void set_d3q19(orc_sim *s) {
+  /* rest (1/3), 6 face neighbours (1/18), 12 edge neighbours (1/36) */
+  int q = 0;
+  for (int cz = -1; cz <= 1; ++cz)
+    for (int cy = -1; cy <= 1; ++cy)
+      for (int cx = -1; cx <= 1; ++cx) {
+        int len2 = cx * cx + cy * cy + cz * cz;
+        if (len2 == 3) continue; /* corners are not in D3Q19 */
+        s->ci[q][0] = cx;
+        s->ci[q][1] = cy;
+        s->ci[q][2] = cz;
+        s->wi[q] = len2 == 0 ? 1.0 / 3.0 : (len2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        ++q;
+      }
+  s->Q = q; /* 19 */
+}
+
+static void set_opposites(orc_sim *s) {
+  for (int i = 0; i < s->Q; ++i)
+    for (int j = 0; j < s->Q; ++j)
+      if (s->ci[j][0] == -s->ci[i][0] && s->ci[j][1] == -s->ci[i][1] &&
+          s->ci[j][2] == -s->ci[i][2])
+        s->opp[i] = j;
+}
+
+/* ---- small helpers ---- */
+
+static size_t node_index(const orc_sim *s, int x, int y, int z) {
+  return ((size_t)z * s->n[1] + y) * s->n[0] + x;
+}
+
+static void node_coords(const orc_sim *s, size_t k, int xyz[3]) {
+  xyz[0] = (int)(k % s->n[0]);
+  xyz[1] = (int)((k / s->n[0]) % s->n[1]);
+  xyz[2] = (int)(k / ((size_t)s->n[0] * s->n[1]));
+}
+
+static int wrap(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+static int vertical_walls(const orc_sim *s) { return !(s->p.flags & ORC_PERIODIC_VERTICAL); }
+
+/* Buoyancy + external body force at a node: F = body - A c e_v, A = g (rho_p - rho_0)/rho_0
+ * (Eq. forceterm with the sugar term dropped and phi read as c). */
+static void node_force(const orc_sim *s, double cval, double F[3]) {
+  for (int d = 0; d < 3; ++d) F[d] = s->p.body_force[d];
+  F[s->vaxis] -= s->p.gravity * s->p.density_contrast * cval;
+}
+
+/* ---- a1 + a2: moments and BGK-Guo collision at every node ---- */
+
+static void collide_all(orc_sim *s) {
+  const int Q = s->Q, dim = s->p.dim;
+  const size_t nn = s->nn;
+  const double tau = s->p.tau, cs2 = 1.0 / 3.0;
+#pragma omp parallel for schedule(static)
+  for (long long kk = 0; kk < (long long)nn; ++kk) {
+    size_t k = (size_t)kk;
+    double F[3];
+    node_force(s, s->c[k], F);
+    double rho = 0.0, mom[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+      double fi = s->f[(size_t)i * nn + k];
+      rho += fi;
+      for (int d = 0; d < 3; ++d) mom[d] += fi * s->ci[i][d];
+    }
+    double u[3];
+    for (int d = 0; d < 3; ++d) u[d] = (mom[d] + 0.5 * F[d]) / rho; /* Guo: b = 1/2 */
+    s->rho[k] = rho;
+    for (int d = 0; d < dim; ++d) s->u[(size_t)d * nn + k] = u[d];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; ++i) {
+      double cu = s->ci[i][0] * u[0] + s->ci[i][1] * u[1] + s->ci[i][2] * u[2];
+      double feq = s->wi[i] * rho * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+      /* Guo source: (1 - 1/(2 tau)) w_i [ (c_i - u)/cs2 + (c_i.u) c_i / cs2^2 ] . F */
+      double src = 0.0;
+      for (int d = 0; d < 3; ++d)
+        src += ((s->ci[i][d] - u[d]) / cs2 + cu * s->ci[i][d] / (cs2 * cs2)) * F[d];
+      src *= (1.0 - 1.0 / (2.0 * tau)) * s->wi[i];
+      double fi = s->f[(size_t)i * nn + k];
+      s->fpost[(size_t)i * nn + k] = fi - (fi - feq) / tau + src;
+    }
+  }
+}
+
+/* ---- a3: streaming with halfway bounce-back ---- */
+
+static void stream_all(orc_sim *s) {
+  const int Q = s->Q;
+  const size_t nn = s->nn;
+  const int walls = vertical_walls(s), va = s->vaxis;
+#pragma omp parallel for schedule(static)
+  for (long long kk = 0; kk < (long long)nn; ++kk) {
+    size_t k = (size_t)kk;
+    int xyz[3];
+    node_coords(s, k, xyz);
+    for (int i = 0; i < Q; ++i) {
+      int to[3];
+      int hits_wall = 0;
+      for (int d = 0; d < 3; ++d) {
+        to[d] = xyz[d] + s->ci[i][d];
+        if (d == va && walls && (to[d] < 0 || to[d] >= s->n[d]))
+          hits_wall = 1;
+        else
+          to[d] = wrap(to[d], s->n[d]);
+      }
+      double v = s->fpost[(size_t)i * nn + k];
+      if (hits_wall) /* reflected back to the node it left, reversed */
+        s->f[(size_t)s->opp[i] * nn + k] = v;
+      else
+        s->f[(size_t)i * nn + node_index(s, to[0], to[1], to[2])] = v;
+    }
+  }
+}
+
+/* ---- a5: one WENO5-JS reconstruction, upwind side on the left ----
+ * v[0..4] are the split-flux values at i-2 .. i+2; the result approximates the
+ * flux at the face i+1/2.  Candidate third-order fluxes on the three sub-stencils,
+ * Jiang-Shu smoothness indicators, linear weights (1/10, 6/10, 3/10), and
+ * nonlinear weights d_k/(eps + beta_k)^2 normalised to sum to one (S15-S16). */
+double orc_weno5_left(const double v[5], double eps) {
+  const double a = v[0], b = v[1], c = v[2], d = v[3], e = v[4];
+  double q[3], beta[3];
+  q[0] = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  q[1] = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  q[2] = (2.0 * c + 5.0 * d - e) / 6.0;
+  beta[0] = 13.0 / 12.0 * (a - 2.0 * b + c) * (a - 2.0 * b + c) +
+            0.25 * (a - 4.0 * b + 3.0 * c) * (a - 4.0 * b + 3.0 * c);
+  beta[1] = 13.0 / 12.0 * (b - 2.0 * c + d) * (b - 2.0 * c + d) + 0.25 * (b - d) * (b - d);
+  beta[2] = 13.0 / 12.0 * (c - 2.0 * d + e) * (c - 2.0 * d + e) +
+            0.25 * (3.0 * c - 4.0 * d + e) * (3.0 * c - 4.0 * d + e);
+  const double lin[3] = {0.1, 0.6, 0.3};
+  double wt[3], sum = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    wt[k] = lin[k] / ((eps + beta[k]) * (eps + beta[k]));
+    sum += wt[k];
+  }
+  double h = 0.0;
+  for (int k = 0; k < 3; ++k) h += wt[k] / sum * q[k];
+  return h;
+}
+
+/* Vertical ghost handling: index reflected into the fluid and whether it was a ghost. */
+static int reflect_vertical(int v, int n, int *ghost) {
+  *ghost = 0;
+  if (v < 0) {
+    *ghost = 1;
+    return -1 - v;
+  }
+  if (v >= n) {
+    *ghost = 1;
+    return 2 * n - 1 - v;
+  }
+  return v;
+}
+
+/* ---- a4-a6: total flux through the face between node k and its +1 neighbour along axis d.
+ * The caller never asks for the wall faces. */
+static double face_flux(const orc_sim *s, const double *c, int xyz[3], int d) {
+  const size_t nn = s->nn;
+  const int va = s->vaxis;
+  const int walls = vertical_walls(s) && d == va;
+  double hp[6], hm[6], cv[6];
+  for (int m = -2; m <= 3; ++m) {
+    int p[3] = {xyz[0], xyz[1], xyz[2]};
+    int ghost = 0;
+    if (walls)
+      p[d] = reflect_vertical(xyz[d] + m, s->n[d], &ghost);
+    else
+      p[d] = wrap(xyz[d] + m, s->n[d]);
+    size_t k = node_index(s, p[0], p[1], p[2]);
+    double cval = c[k];
+    double ud = s->u[(size_t)d * nn + k];
+    if (ghost) ud = -ud; /* no-slip wall: velocity odd about the wall */
+    double w = ud - (d == va ? s->p.settling_velocity : 0.0);
+    cv[m + 2] = cval;
+    hp[m + 2] = 0.5 * (w + s->alpha) * cval;
+    hm[m + 2] = 0.5 * (w - s->alpha) * cval;
+  }
+  /* h+ : upwind from the left, points i-2..i+2 */
+  double fplus = orc_weno5_left(hp, s->eps);
+  /* h- : mirror image, points i+3..i-1 read right to left */
+  const double mirror[5] = {hm[5], hm[4], hm[3], hm[2], hm[1]};
+  double fminus = orc_weno5_left(mirror, s->eps);
+  /* a6: central diffusion, flux = -kappa dc/dx at the face */
+  double fdiff = -s->p.diffusivity * (cv[3] - cv[2]);
+  return fplus + fminus + fdiff;
+}
+
+/* ---- a7: L(c) = -div(flux), conservative form ---- */
+
+static void transport_rate(orc_sim *s, const double *c, double *L) {
+  const size_t nn = s->nn;
+  const int dim = s->p.dim, va = s->vaxis, walls = vertical_walls(s);
+  for (size_t k = 0; k < nn; ++k) L[k] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    /* flux[k] = flux through the face on the + side of node k along d */
+#pragma omp parallel for schedule(static)
+    for (long long kk = 0; kk < (long long)nn; ++kk) {
+      size_t k = (size_t)kk;
+      int xyz[3];
+      node_coords(s, k, xyz);
+      if (d == va && walls && xyz[d] == s->n[d] - 1)
+        s->flux[k] = 0.0; /* lid: no flux */
+      else
+        s->flux[k] = face_flux(s, c, xyz, d);
+    }
+#pragma omp parallel for schedule(static)
+    for (long long kk = 0; kk < (long long)nn; ++kk) {
+      size_t k = (size_t)kk;
+      int xyz[3];
+      node_coords(s, k, xyz);
+      double fminus;
+      if (d == va && walls && xyz[d] == 0) {
+        fminus = -s->p.settling_velocity * c[k]; /* floor: settling outflow */
+      } else {
+        int p[3] = {xyz[0], xyz[1], xyz[2]};
+        p[d] = wrap(xyz[d] - 1, s->n[d]);
+        fminus = s->flux[node_index(s, p[0], p[1], p[2])];
+      }
+      L[k] -= s->flux[k] - fminus;
+    }
+  }
+}
+
+/* Sum of c over the floor row/plane (v = 0), serial and in index order. */
+static double floor_sum(const orc_sim *s, const double *c) {
+  double acc = 0.0;
+  if (s->p.dim == 2) {
+    for (int x = 0; x < s->n[0]; ++x) acc += c[node_index(s, x, 0, 0)];
+  } else {
+    for (int y = 0; y < s->n[1]; ++y)
+      for (int x = 0; x < s->n[0]; ++x) acc += c[node_index(s, x, y, 0)];
+  }
+  return acc;
+}
+
+/* ---- a8 + a9: SSP-RK3 (S21-S23) with dt = 1, velocity frozen, deposit by b-weights ---- */
+
+static void rk3_transport(orc_sim *s) {
+  const size_t nn = s->nn;
+  double *c = s->c, *c1 = s->c1, *c2 = s->c2, *L = s->L;
+  transport_rate(s, c, L);
+  for (size_t k = 0; k < nn; ++k) c1[k] = c[k] + L[k];
+  transport_rate(s, c1, L);
+  for (size_t k = 0; k < nn; ++k) c2[k] = 0.75 * c[k] + 0.25 * c1[k] + 0.25 * L[k];
+  double dep = 0.0;
+  if (vertical_walls(s))
+    dep = s->p.settling_velocity *
+          (floor_sum(s, c) / 6.0 + floor_sum(s, c1) / 6.0 + 2.0 * floor_sum(s, c2) / 3.0);
+  transport_rate(s, c2, L);
+  for (size_t k = 0; k < nn; ++k) c[k] = c[k] / 3.0 + 2.0 * c2[k] / 3.0 + 2.0 * L[k] / 3.0;
+  s->deposit += dep;
+}
+
+static void check_state(orc_sim *s) {
+  const size_t nn = s->nn;
+  for (size_t k = 0; k < nn; ++k) {
+    if (!isfinite(s->c[k])) s->status = ORC_EUNSTABLE;
+    for (int d = 0; d < s->p.dim; ++d) {
+      double ud = s->u[(size_t)d * nn + k];
+      if (!isfinite(ud) || fabs(ud) > s->p.u_cap) s->status = ORC_EUNSTABLE;
+    }
+  }
+}
+
+/* ---- public entry points (ctypes) ---- */
+
+orc_sim *orc_create(const orc_params *p) {
+  if (!p || (p->dim != 2 && p->dim != 3) || p->nx < 4 || p->ny < 4 || p->tau <= 0.5) return NULL;
+  if (p->dim == 3 && p->nz < 4) return NULL;
+  orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+  if (!s) return NULL;
+  s->p = *p;
+  if (s->p.dim == 2) s->p.nz = 1;
+  if (s->p.u_cap <= 0.0) s->p.u_cap = 0.1;
+  s->n[0] = s->p.nx;
+  s->n[1] = s->p.ny;
+  s->n[2] = s->p.nz;
+  s->vaxis = s->p.dim - 1;
+  s->nn = (size_t)s->n[0] * s->n[1] * s->n[2];
+  s->alpha = s->p.lf_alpha > 0.0 ? s->p.lf_alpha : s->p.settling_velocity + s->p.u_cap;
+  s->eps = 1e-6 * s->alpha * s->alpha;
+  if (s->p.dim == 2)
+    set_d2q9(s);
+  else
+    set_d3q19(s);
+  set_opposites(s);
+  const size_t nn = s->nn;
+  s->f = (double *)calloc((size_t)s->Q * nn, sizeof(double));
+  s->fpost = (double *)calloc((size_t)s->Q * nn, sizeof(double));
+  s->c = (double *)calloc(nn, sizeof(double));
+  s->c1 = (double *)calloc(nn, sizeof(double));
+  s->c2 = (double *)calloc(nn, sizeof(double));
+  s->L = (double *)calloc(nn, sizeof(double));
+  s->flux = (double *)calloc(nn, sizeof(double));
+  s->rho = (double *)calloc(nn, sizeof(double));
+  s->u = (double *)calloc((size_t)s->p.dim * nn, sizeof(double));
+  if (!s->f || !s->fpost || !s->c || !s->c1 || !s->c2 || !s->L || !s->flux || !s->rho || !s->u) {
+    free(s->f); free(s->fpost); free(s->c); free(s->c1); free(s->c2);
+    free(s->L); free(s->flux); free(s->rho); free(s->u); free(s);
+    return NULL;
+  }
+  return s;
+}
+
+void orc_destroy(orc_sim *s) {
+  if (!s) return;
+  free(s->f); free(s->fpost); free(s->c); free(s->c1); free(s->c2);
+  free(s->L); free(s->flux); free(s->rho); free(s->u);
+  free(s);
+}
+
+/* c0[nn] required.  u0[dim*nn] optional: populations start at equilibrium
+ * f_i = f_i^eq(rho = 1, u0) (or f_i = w_i when u0 is NULL). */
+int orc_init(orc_sim *s, const double *c0, const double *u0) {
+  if (!s || !c0) return ORC_EINVAL;
+  const size_t nn = s->nn;
+  const double cs2 = 1.0 / 3.0;
+  memcpy(s->c, c0, nn * sizeof(double));
+  for (size_t k = 0; k < nn; ++k) {
+    double u[3] = {0.0, 0.0, 0.0};
+    if (u0)
+      for (int d = 0; d < s->p.dim; ++d) u[d] = u0[(size_t)d * nn + k];
+    for (int d = 0; d < s->p.dim; ++d) s->u[(size_t)d * nn + k] = u[d];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < s->Q; ++i) {
+      double cu = s->ci[i][0] * u[0] + s->ci[i][1] * u[1] + s->ci[i][2] * u[2];
+      s->f[(size_t)i * nn + k] =
+          s->wi[i] * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+    }
+    s->rho[k] = 1.0;
+  }
+  s->deposit = 0.0;
+  s->steps = 0;
+  s->status = ORC_OK;
+  return ORC_OK;
+}
+
+/* One coupled step = a1..a3 on the populations (unless the velocity is frozen),
+ * then a4..a9 on c with the velocity of a1 (O7: u at time n, frozen over the stages). */
+int orc_step(orc_sim *s, int64_t nsteps) {
+  if (!s) return ORC_EINVAL;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (!(s->p.flags & ORC_FROZEN_VELOCITY)) {
+      collide_all(s);
+      stream_all(s);
+    }
+    rk3_transport(s);
+    check_state(s);
+    s->steps++;
+  }
+  return s->status;
+}
+
+/* Macroscopic fields of the current state: rho, the half-force-corrected
+ * velocity u = (sum f c + F/2)/rho computed with the current c, and c.
+ * With a frozen velocity, rho = 1 and u is the frozen field.  Any pointer may be NULL. */
+void orc_fields(const orc_sim *s, double *rho, double *u, double *c) {
+  const size_t nn = s->nn;
+  for (size_t k = 0; k < nn; ++k) {
+    if (s->p.flags & ORC_FROZEN_VELOCITY) {
+      if (rho) rho[k] = 1.0;
+      if (u)
+        for (int d = 0; d < s->p.dim; ++d) u[(size_t)d * nn + k] = s->u[(size_t)d * nn + k];
+    } else {
+      double F[3];
+      node_force(s, s->c[k], F);
+      double r = 0.0, mom[3] = {0.0, 0.0, 0.0};
+      for (int i = 0; i < s->Q; ++i) {
+        double fi = s->f[(size_t)i * nn + k];
+        r += fi;
+        for (int d = 0; d < 3; ++d) mom[d] += fi * s->ci[i][d];
+      }
+      if (rho) rho[k] = r;
+      if (u)
+        for (int d = 0; d < s->p.dim; ++d) u[(size_t)d * nn + k] = (mom[d] + 0.5 * F[d]) / r;
+    }
+    if (c) c[k] = s->c[k];
+  }
+}
+
+/* Raw population sums over the domain: out[0] = sum f, out[1..3] = sum f c_i (serial). */
+void orc_population_moments(const orc_sim *s, double out[4]) {
+  const size_t nn = s->nn;
+  out[0] = out[1] = out[2] = out[3] = 0.0;
+  for (size_t k = 0; k < nn; ++k)
+    for (int i = 0; i < s->Q; ++i) {
+      double fi = s->f[(size_t)i * nn + k];
+      out[0] += fi;
+      for (int d = 0; d < 3; ++d) out[1 + d] += fi * s->ci[i][d];
+    }
+}
+
+double orc_deposit(const orc_sim *s) { return s->deposit; }
+int64_t orc_steps(const orc_sim *s) { return s->steps; }
+double orc_alpha(const orc_sim *s) { return s->alpha; }
+
+/* Total c over the domain, serial and in index order. */
+double orc_total_mass(const orc_sim *s) {
+  double acc = 0.0;
+  for (size_t k = 0; k < s->nn; ++k) acc += s->c[k];
+  return acc;
+}
+
+/* L(c) for a given c and transport velocity u (dim*nn), using the walls and
+ * parameters of the simulation; used to pin the spatial operator alone. */
+void orc_transport_rate(orc_sim *s, const double *c, const double *u, double *L) {
+  memcpy(s->u, u, (size_t)s->p.dim * s->nn * sizeof(double));
+  transport_rate(s, c, L);
+}
+
+int orc_lattice(const orc_sim *s, int *ci, double *wi) {
+  for (int i = 0; i < s->Q; ++i) {
+    for (int d = 0; d < 3; ++d) ci[3 * i + d] = s->ci[i][d];
+    wi[i] = s->wi[i];
+  }
+  return s->Q;
+}
