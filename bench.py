@@ -1,0 +1,299 @@
+"""Benchmark of the coupled LBM + WENO5 step (GLUPS and fraction of the HBM roofline).
+
+Default workload: 2D D2Q9, 2048 x 4096 lattice, FP32 populations stored as
+f - w_i, FP32 WENO5, A = 1e-5, Vs = 1e-3, kappa = 1e-3, tau = 0.6; synthetic tanh
+interface at 0.75 H with a seeded U(-1e-3, 1e-3) perturbation.  One "step" is one
+full coupled time step over the whole lattice.  GLUPS = nodes x steps / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU): independent replicas, one per GPU, no
+collective on the data path; the value is the sum over ranks (weak scaling).
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2106_07694_gb300 import workloads  # noqa: E402
+
+WL = workloads.MAIN_2D
+METRIC = "coupled LBM+WENO5 GLUPS (2D D2Q9 2048x4096 FP32)"
+UNIT = "GLUPS"
+
+
+def phys_kwargs(wl):
+    return dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
+                settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_sample(wl, steps, threads):
+    """Time the FP64 CPU oracle on the full lattice for `steps` steps (after 1 warm-up)."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import oracle
+    s = oracle.OracleSim(wl.shape, **phys_kwargs(wl))
+    s.init(wl.initial_c())
+    s.step(1)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return wl.nodes * steps / dt / 1e9, dt
+
+
+def bench_reference(args):
+    """The oracle as it stands, on the host cores.  Each step is one full coupled step
+    of a bounded sample of the workload: the full 2048-wide lattice cut to 128 rows
+    (same physics, interface at 0.75 of the band), so K steps end within minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import oracle
+    band = WL.with_(shape=(WL.shape[0], 128))
+    s = oracle.OracleSim(band.shape, **phys_kwargs(band))
+    s.init(band.initial_c())
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    total = time.perf_counter() - t0
+    value = band.nodes * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WL.name, "nx": WL.shape[0], "ny": WL.shape[1],
+                                        "lattice": "D2Q9", "host_threads": threads,
+                                        "sample_rows": band.shape[1]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"FP64 C oracle, {band.shape[0]}x{band.shape[1]} band of the "
+                                   f"workload, {args.steps} steps after {args.warmup} warm-up"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2106_07694_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = WL
+    kw = phys_kwargs(wl)
+    stream = torch.cuda.current_stream()
+    sim = lw.Simulation(wl.shape, fp64=False, stream=stream, **kw)
+    c0 = wl.initial_c().astype(np.float32)
+    sim.init(torch.from_numpy(c0).to(dev))
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K coupled steps, production path (CUDA graphs), inputs resident
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = lw.lbm_wenoc_launch_count(sim.handle)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = lw.lbm_wenoc_launch_count(sim.handle) - launches0
+    st = sim.status()
+    if st != lw.LW_OK:
+        raise RuntimeError(f"device status {st} after the timed region")
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * wl.nodes * args.steps / (t_max * 1e-3) / 1e9
+
+    # ---- per-kernel durations: the same K steps again, CUDA events around each launch
+    lw.lbm_wenoc_profile_enable(sim.handle, True)
+    lw.lbm_wenoc_profile_read(sim.handle, reset=True)
+    sim.step(args.steps)
+    stats = lw.lbm_wenoc_profile_read(sim.handle, reset=True)
+    lw.lbm_wenoc_profile_enable(sim.handle, False)
+    kernels = {k: {"launches": n, "avg_us": 1e3 * t / max(n, 1), "share": None} for k, (n, t) in stats.items()}
+    tot = sum(t for (_, t) in stats.values())
+    for k, (n, t) in stats.items():
+        kernels[k]["share"] = t / tot if tot > 0 else None
+    dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
+    peak, peak_kind = load_peaks()
+    # Algorithmic bytes per node of each kernel family (FP32): populations in+out and c in
+    # for the fluid kernel; c in + c out for the fused transport; per-stage kernels read the
+    # stage input and write the stage output.
+    alg_bytes = {"lbm_collide_stream": 2 * 9 * 4 + 4, "rk3_sweep2d": 8, "rk_stage1": 8, "rk_stage2": 12,
+                 "rk_stage3": 12}
+    roofline = None
+    if dominant in alg_bytes:
+        avg_s = stats[dominant][1] * 1e-3 / stats[dominant][0]
+        achieved = alg_bytes[dominant] * wl.nodes / avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                    "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                    "alg_bytes_per_node": alg_bytes[dominant]}
+    step_ms = t_max / args.steps
+    step_roofline = {"alg_bytes_per_node": 80, "achieved_GBs": 80 * wl.nodes / (step_ms * 1e-3) / 1e9,
+                     "frac_of_measured_hbm": 80 * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
+
+    # ---- end to end through the C ABI with host buffers: H2D of c0 (pinned), init,
+    # K steps, deposit read and D2H of the final c field, all inside the timed region
+    c_host = torch.from_numpy(c0).pin_memory()
+    c_out = torch.empty_like(c_host).pin_memory()
+    sim2 = lw.Simulation(wl.shape, fp64=False, stream=stream, **kw)
+    sim2.init(c_host)
+    sim2.step(1)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    sim2.init(c_host)
+    sim2.step(args.steps)
+    dep = sim2.deposit
+    lw.lbm_wenoc_fields(sim2.handle, None, None, c_out)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * wl.nodes * args.steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": c_host.numel() * 4 / args.steps,
+           "d2h_bytes_per_step": (c_out.numel() * 4 + 8) / args.steps,
+           "note": "per job: H2D c0 + init + K steps + deposit (8 B) + D2H c, host wall clock"}
+    assert np.isfinite(dep)
+    sim2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, dt = run_oracle_sample(wl, args.cpu_steps, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 C oracle on the full {wl.shape[0]}x{wl.shape[1]} lattice, "
+                         f"{args.cpu_steps} steps after 1 warm-up ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "nx": wl.shape[0], "ny": wl.shape[1], "lattice": "D2Q9",
+                       "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
+                       "kappa": wl.diffusivity, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (populations 302 MB)"},
+            "roofline": roofline, "step_roofline": step_roofline, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,138 @@
+/*
+ * lbm_wenoc: one-GPU (GB300, sm_103a) coupled lattice-Boltzmann + WENO5 solver
+ * for a settling particle concentration c in a Boussinesq fluid.
+ *
+ * The problem follows the paper's statement (arXiv 2106.07694):
+ *   fluid      BGK lattice Boltzmann, D2Q9 (2D) or D3Q19 (3D), relaxation time tau
+ *              with nu = (tau - 1/2)/3 (Sec. 2.3.1, Eqs. LBE, tau), Guo forcing
+ *              (Eq. LBE_Guo), no-slip floor and lid by halfway bounce-back, periodic
+ *              sides (Sec. 2.2.1);
+ *   force      F = -A c e_v + body_force, A = gravity * density_contrast
+ *              (Eq. forceterm with the density-altering scalar left out);
+ *   particles  dc/dt + div[c (u - Vs e_v)] = kappa lap c (Eq. ADS), WENO5 with a
+ *              global Lax-Friedrichs flux split, central diffusion, SSP-RK3
+ *              (Supplement Sec. 1, Eqs. S4, S8-S23); the settling flux through the
+ *              floor leaves the domain and is accumulated as deposited mass
+ *              (Sec. 4, m_b).
+ * Lattice units: dx = dt = 1.  e_v is the vertical axis: y in 2D, z in 3D.
+ *
+ * Memory: every device buffer belongs to the caller.  The library keeps only a
+ * host-side handle (and the CUDA graphs and events it creates) and never calls
+ * cudaMalloc.  All arrays are dense, C order, vertical axis slowest:
+ * index = (z*ny + y)*nx + x.  Vectors are component-major: u[d*n + index].
+ * The element type of c and u buffers is double when LW_FP64 is set, else float.
+ *
+ * Errors: every int-returning call returns LW_OK (0) or a negative LW_E* code;
+ * nothing aborts, throws or traps across this boundary.  Work is asynchronous on
+ * the stream given at create unless a call says it synchronises.
+ * Threading: a handle is not thread-safe; use one handle per host thread/stream.
+ */
+#ifndef LBM_WENOC_H
+#define LBM_WENOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LW_OK 0
+#define LW_EINVAL -1    /* bad argument or parameter (e.g. tau <= 1/2, nx % 4 != 0) */
+#define LW_ENOMEM -2    /* workspace smaller than lbm_wenoc_workspace_bytes() */
+#define LW_ECUDA -3     /* a CUDA runtime call failed */
+#define LW_EUNSTABLE -4 /* device status: non-finite value or |u_d| > u_cap */
+#define LW_ETIMEOUT -5  /* a bounded device wait gave up */
+#define LW_ESTATE -6    /* call out of order (e.g. step before init) */
+
+#define LW_FP64 0x1u              /* FP64 populations and arithmetic (validation build) */
+#define LW_PERIODIC_VERTICAL 0x2u /* vertical axis periodic too: no walls, no deposit (tests) */
+#define LW_FROZEN_VELOCITY 0x4u   /* fluid not advanced; c transported by the u given at init (tests) */
+#define LW_NO_GRAPH 0x8u          /* launch kernels one by one instead of replaying CUDA graphs */
+
+typedef struct lbm_wenoc lbm_wenoc; /* opaque host-side handle */
+
+typedef struct {
+  int32_t dim;               /* 2 (D2Q9) or 3 (D3Q19) */
+  int32_t nx, ny, nz;        /* lattice extents; nz ignored in 2D; nx % 4 == 0, ny >= 4, nz >= 4 in 3D */
+  double tau;                /* BGK relaxation time, > 1/2 (Eq. tau) */
+  double gravity;            /* g, lattice units */
+  double density_contrast;   /* (rho_p - rho_0)/rho_0; force = -gravity*density_contrast*c e_v (Eq. forceterm) */
+  double settling_velocity;  /* Vs >= 0, directed down (Eq. ADS) */
+  double diffusivity;        /* kappa >= 0 (D_c of Eq. ADS) */
+  double lf_alpha;           /* Lax-Friedrichs split speed; 0 selects settling_velocity + u_cap */
+  double u_cap;              /* bound on |u_d| checked on the device; 0 selects 0.1 */
+  double body_force[3];      /* extra uniform force (e.g. a channel flow), added to the buoyancy */
+  uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH */
+} lbm_wenoc_params;
+
+/* Bytes of device workspace a handle with these parameters needs (populations,
+ * concentration, two Runge-Kutta stage fields, velocity, reduction scratch). */
+int lbm_wenoc_workspace_bytes(const lbm_wenoc_params* p, size_t* bytes);
+
+/* Create a handle over a caller-owned device workspace (256-byte aligned, at least
+ * lbm_wenoc_workspace_bytes() long, kept alive until destroy).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream); all work of the handle runs on it.
+ * The handle binds to the current device.  Returns LW_EINVAL / LW_ENOMEM on bad input. */
+int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t bytes,
+                     void* cuda_stream, lbm_wenoc** out);
+
+/* Set the initial state (Sec. 2.2.1, Eqs. ini1/ini: fluid at rest, c given):
+ * c0[n] is required; u0[dim*n] is optional (NULL = fluid at rest).  Populations
+ * start at equilibrium f_i = f_i^eq(rho = 1, u0).  Either pointer may be host or
+ * device memory (detected); host data are copied on the stream, so a pageable host
+ * buffer may be reused when the call returns.  Resets the deposit and the step count. */
+int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0);
+
+/* Advance nsteps >= 0 coupled time steps (asynchronous): per step, moments with the
+ * half force, BGK-Guo collision and in-place streaming with bounce-back, then three
+ * SSP-RK3 stages of the WENO5 transport of c with the velocity of that step, and the
+ * deposit through the floor.  Returns LW_ESTATE before init. */
+int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps);
+
+/* Synchronise the stream and return the accumulated deposited mass (FP64): the sum
+ * over steps of Vs * sum_floor(c/6 + c1/6 + 2 c2/3), i.e. the RK3-weighted settling
+ * flux through the floor, so that total_mass + deposit is conserved.
+ * Returns LW_EUNSTABLE if the device status word is set. */
+int lbm_wenoc_deposited_mass(lbm_wenoc* h, double* out);
+
+/* Synchronise and return sum of c over the domain (FP64, fixed summation order). */
+int lbm_wenoc_total_mass(lbm_wenoc* h, double* out);
+
+/* Write the macroscopic state of the current step: rho[n], u[dim*n] (half-force
+ * corrected velocity (sum f c + F/2)/rho with the current c), c[n].  Any pointer may
+ * be NULL; each may be host or device memory.  Synchronises. */
+int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c);
+
+/* Synchronise and return LW_OK or LW_EUNSTABLE from the device status word. */
+int lbm_wenoc_status(lbm_wenoc* h);
+
+/* Steps taken since init. */
+int64_t lbm_wenoc_steps(const lbm_wenoc* h);
+
+/* Per-kernel timing with CUDA events on the handle's stream (off by default).
+ * enable != 0 records an event pair around every kernel launched by later calls. */
+int lbm_wenoc_profile_enable(lbm_wenoc* h, int enable);
+
+typedef struct {
+  char name[48];    /* kernel family name */
+  int64_t launches; /* launches recorded */
+  double total_ms;  /* summed device time between the event pairs */
+} lbm_wenoc_kernel_stat;
+
+/* Synchronise, fold pending event pairs into per-kernel totals, copy up to max
+ * entries into out, set *count; reset = 1 clears the totals afterwards. */
+int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, int* count,
+                           int reset);
+
+/* Number of kernel launches this handle has issued since create. */
+int64_t lbm_wenoc_launch_count(const lbm_wenoc* h);
+
+/* Destroy the handle (graphs, events).  Does not free the caller's workspace. */
+void lbm_wenoc_destroy(lbm_wenoc* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_WENOC_H */

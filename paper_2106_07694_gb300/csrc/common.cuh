@@ -1,0 +1,56 @@
+// Shared device-side argument block and small helpers of the lbm_wenoc kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lw {
+
+// Status bits ORed by kernels into the device status word.
+constexpr unsigned kStatusUnstable = 1u;  // non-finite value or |u_d| > u_cap
+constexpr unsigned kStatusTimeout = 2u;   // a bounded wait gave up
+
+template <typename T>
+struct Args {
+  T* g;    // populations stored as g_i = f_i - w_i, SoA: g[i*n + node]
+  T* c;    // concentration c^n (updated in place by the last RK stage)
+  T* c1;   // RK stage 1 field
+  T* c2;   // RK stage 2 field
+  T* u;    // transport velocity of the current step, u[d*n + node]
+  double* partials;  // per-block FP64 partial sums (fixed-order reductions)
+  double* scalars;   // [0] deposit, [1] reduction result
+  unsigned* status;  // status word
+  unsigned* ticket;  // last-block ticket of the reductions
+  int nx, ny, nz;    // extents (nz = 1 in 2D)
+  long long n;       // nodes
+  int walls;         // 1 = no-slip floor and lid, 0 = periodic vertical
+  T omega;           // 1/tau
+  T guo;             // 1 - 1/(2 tau)
+  T A;               // gravity * density_contrast
+  T bf[3];           // body force
+  T vs;              // settling velocity
+  T kappa;           // diffusivity
+  T alpha;           // Lax-Friedrichs split speed
+  T inv_alpha;
+  T u_cap;
+};
+
+__device__ __forceinline__ int wrap_dec(int a, int n) { return a < 0 ? a + n : a; }
+__device__ __forceinline__ int wrap_inc(int a, int n) { return a >= n ? a - n : a; }
+__device__ __forceinline__ int wrap_any(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
+
+// Flag a bad value once per warp (no trap, no assert: the host reads the word).
+__device__ __forceinline__ unsigned lane_id() {
+  unsigned l;
+  asm volatile("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+
+__device__ __forceinline__ void report_status(unsigned* status, bool bad) {
+  unsigned m = __ballot_sync(__activemask(), bad);
+  if (m != 0u && lane_id() == (unsigned)(__ffs(m) - 1)) atomicOr(status, kStatusUnstable);
+}
+
+}  // namespace lw

@@ -1,0 +1,197 @@
+// Fluid half of the coupled step: moments with the half force, BGK collision with
+// the Guo source, streaming with halfway bounce-back -- fused in one in-place pass
+// over a single population array with the AA access pattern.
+//
+//   a1  rho = 1 + sum g_i,  rho u = sum g_i c_i + F/2,  F = body - A c e_v
+//       (Sec. 2.3.1, Eqs. dens, mom_dens; rho u* of Eq. LBE_Guo with b = 1/2)
+//   a2  g_i* = g_i - (g_i - g_i^eq)/tau + (1 - 1/(2 tau)) w_i [3(c_i - u) + 9 (c_i.u) c_i].F
+//       (Eqs. LBE, LBE_Guo; Guo 2002 source; g = f - w_i so that FP32 keeps the
+//       small deviations from rest)
+//   a3  streaming along c_i; populations that would cross the floor or lid are
+//       reflected back to the node they left (halfway bounce-back, no-slip walls).
+//
+// AA pattern: one array, no second copy.  On an even step a node reads its own
+// slots and writes the post-collision g_i* into slot opp(i) of the same node.  On an
+// odd step it pulls g_i from slot opp(i) of node x - c_i (slot i of itself when
+// x - c_i is behind a wall) and pushes g_i* to slot i of x + c_i (slot opp(i) of
+// itself when x + c_i is behind a wall).  Every location is read and written by
+// one thread only, so the pass is in place.  After an odd number of steps the
+// array holds post-collision values (parity 1); after an even number it holds the
+// streamed populations (parity 0).
+#pragma once
+#include "common.cuh"
+#include "lattice.cuh"
+
+namespace lw {
+
+// Neighbour of (x,y,z) along direction i, sign s = +1 (x + c_i) or -1 (x - c_i).
+// Returns false when the neighbour is behind a no-slip wall.
+template <class LAT>
+__device__ __forceinline__ bool neighbour(int i, int s, int x, int y, int z, int nx, int ny, int nz,
+                                          bool walls, long long& out) {
+  int xx = wrap_any(x + s * LAT::cx(i), nx);
+  int yy = y + s * LAT::cy(i);
+  int zz = z + s * LAT::cz(i);
+  if (LAT::VAXIS == 1) {
+    if (yy < 0 || yy >= ny) {
+      if (walls) return false;
+      yy = wrap_any(yy, ny);
+    }
+  } else {
+    yy = wrap_any(yy, ny);
+    if (zz < 0 || zz >= nz) {
+      if (walls) return false;
+      zz = wrap_any(zz, nz);
+    }
+  }
+  out = ((long long)zz * ny + yy) * nx + xx;
+  return true;
+}
+
+// Load the populations of node (x,y,z) as they stand at the start of a step with
+// the given parity (0: natural layout; 1: post-collision layout, pull from neighbours).
+template <class LAT, typename T, int PARITY>
+__device__ __forceinline__ void load_populations(const Args<T>& a, int x, int y, int z, long long node,
+                                                 T (&g)[LAT::Q]) {
+  const long long n = a.n;
+#pragma unroll
+  for (int i = 0; i < LAT::Q; ++i) {
+    if (PARITY == 0) {
+      g[i] = a.g[i * n + node];
+    } else {
+      long long src;
+      if (neighbour<LAT>(i, -1, x, y, z, a.nx, a.ny, a.nz, a.walls != 0, src))
+        g[i] = a.g[LAT::opp(i) * n + src];
+      else
+        g[i] = a.g[i * n + node];
+    }
+  }
+}
+
+template <class LAT, typename T>
+__device__ __forceinline__ void node_force(const Args<T>& a, T cval, T (&F)[3]) {
+  F[0] = a.bf[0];
+  F[1] = a.bf[1];
+  F[2] = a.bf[2];
+  F[LAT::VAXIS] -= a.A * cval;
+}
+
+template <class LAT, typename T, int PARITY>
+__global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx) return;
+  const long long n = a.n;
+  const long long node = ((long long)z * a.ny + y) * a.nx + x;
+
+  T g[LAT::Q];
+  load_populations<LAT, T, PARITY>(a, x, y, z, node, g);
+
+  // a1: moments (rho - 1 and momentum of g; sum w_i c_i = 0) and the force from c^n
+  T drho = T(0), j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < LAT::Q; ++i) {
+    drho += g[i];
+    if (LAT::cx(i)) j[0] += LAT::cx(i) * g[i];
+    if (LAT::cy(i)) j[1] += LAT::cy(i) * g[i];
+    if (LAT::cz(i)) j[2] += LAT::cz(i) * g[i];
+  }
+  T F[3];
+  node_force<LAT, T>(a, a.c[node], F);
+  const T rho = T(1) + drho;
+  const T inv_rho = T(1) / rho;
+  T u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = (j[d] + T(0.5) * F[d]) * inv_rho;
+  bool bad = !finite_val(rho);
+#pragma unroll
+  for (int d = 0; d < LAT::DIM; ++d) {
+    a.u[d * n + node] = u[d];
+    bad = bad || !(fabs(u[d]) <= a.u_cap);
+  }
+  report_status(a.status, bad);
+
+  // a2: BGK collision with the Guo source, in the g = f - w variables
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+#pragma unroll
+  for (int i = 0; i < LAT::Q; ++i) {
+    const T wi = T(LAT::w(i));
+    const T cu = LAT::cx(i) * u[0] + LAT::cy(i) * u[1] + LAT::cz(i) * u[2];
+    const T cF = LAT::cx(i) * F[0] + LAT::cy(i) * F[1] + LAT::cz(i) * F[2];
+    const T geq = wi * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    const T src = a.guo * wi * (T(3) * (cF - uF) + T(9) * cu * cF);
+    g[i] = g[i] - a.omega * (g[i] - geq) + src;
+  }
+
+  // a3: store (even: swap slots in place; odd: push to neighbours / bounce back)
+#pragma unroll
+  for (int i = 0; i < LAT::Q; ++i) {
+    if (PARITY == 0) {
+      a.g[LAT::opp(i) * n + node] = g[i];
+    } else {
+      long long dst;
+      if (neighbour<LAT>(i, +1, x, y, z, a.nx, a.ny, a.nz, a.walls != 0, dst))
+        a.g[i * n + dst] = g[i];
+      else
+        a.g[LAT::opp(i) * n + node] = g[i];
+    }
+  }
+}
+
+// Macroscopic fields of the current state (parity as in load_populations):
+// rho, u = (sum g c + F/2)/rho with the current c.
+template <class LAT, typename T, int PARITY>
+__global__ void __launch_bounds__(128) fields_kernel(Args<T> a, T* rho_out, T* u_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx) return;
+  const long long n = a.n;
+  const long long node = ((long long)z * a.ny + y) * a.nx + x;
+  T g[LAT::Q];
+  load_populations<LAT, T, PARITY>(a, x, y, z, node, g);
+  T drho = T(0), j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < LAT::Q; ++i) {
+    drho += g[i];
+    j[0] += LAT::cx(i) * g[i];
+    j[1] += LAT::cy(i) * g[i];
+    j[2] += LAT::cz(i) * g[i];
+  }
+  T F[3];
+  node_force<LAT, T>(a, a.c[node], F);
+  const T rho = T(1) + drho;
+  if (rho_out) rho_out[node] = rho;
+  if (u_out) {
+#pragma unroll
+    for (int d = 0; d < LAT::DIM; ++d) u_out[d * n + node] = (j[d] + T(0.5) * F[d]) / rho;
+  }
+}
+
+// Initial state: g_i = f_i^eq(1, u0) - w_i, u = u0 (or 0).  c is already in place.
+template <class LAT, typename T>
+__global__ void __launch_bounds__(128) init_kernel(Args<T> a, const T* u0) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx) return;
+  const long long n = a.n;
+  const long long node = ((long long)z * a.ny + y) * a.nx + x;
+  T u[3] = {T(0), T(0), T(0)};
+  if (u0) {
+#pragma unroll
+    for (int d = 0; d < LAT::DIM; ++d) u[d] = u0[d * n + node];
+  }
+#pragma unroll
+  for (int d = 0; d < LAT::DIM; ++d) a.u[d * n + node] = u[d];
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int i = 0; i < LAT::Q; ++i) {
+    const T cu = LAT::cx(i) * u[0] + LAT::cy(i) * u[1] + LAT::cz(i) * u[2];
+    a.g[i * n + node] = T(LAT::w(i)) * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+  }
+}
+
+}  // namespace lw

@@ -1,0 +1,570 @@
+// Host side of the lbm_wenoc C ABI (include/lbm_wenoc.h): parameter checks, the
+// carve-up of the caller's workspace, kernel launches, CUDA-graph replay of whole
+// steps, FP64 read-backs and per-kernel event timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "lbm_wenoc.h"
+#include "common.cuh"
+#include "lattice.cuh"
+#include "lbm_kernels.cuh"
+#include "reduce_kernels.cuh"
+#include "transport_kernels.cuh"
+#include "transport_sweep2d.cuh"
+
+namespace {
+
+using lw::Args;
+
+constexpr int kLbmThreads = 128;
+
+// Velocity sets must come in opposite pairs with isotropic second moments.
+template <class LAT>
+constexpr bool lattice_ok() {
+  double s = 0, sxx = 0, syy = 0, szz = 0, sxy = 0;
+  for (int i = 0; i < LAT::Q; ++i) {
+    const int o = LAT::opp(i);
+    if (LAT::cx(o) != -LAT::cx(i) || LAT::cy(o) != -LAT::cy(i) || LAT::cz(o) != -LAT::cz(i)) return false;
+    s += LAT::w(i);
+    sxx += LAT::w(i) * LAT::cx(i) * LAT::cx(i);
+    syy += LAT::w(i) * LAT::cy(i) * LAT::cy(i);
+    szz += LAT::w(i) * LAT::cz(i) * LAT::cz(i);
+    sxy += LAT::w(i) * LAT::cx(i) * LAT::cy(i);
+  }
+  auto close = [](double a, double b) { return a - b < 1e-12 && b - a < 1e-12; };
+  return close(s, 1.0) && close(sxx, 1.0 / 3.0) && close(syy, 1.0 / 3.0) && close(sxy, 0.0) &&
+         (LAT::DIM == 2 ? close(szz, 0.0) : close(szz, 1.0 / 3.0));
+}
+static_assert(lattice_ok<D2Q9>(), "D2Q9 table");
+static_assert(lattice_ok<D3Q19>(), "D3Q19 table");
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  size_t g, c, c1, c2, u, partials, scalars, status, total;
+};
+
+Layout make_layout(const lbm_wenoc_params& p) {
+  const size_t n = (size_t)p.nx * p.ny * (p.dim == 3 ? p.nz : 1);
+  const size_t es = (p.flags & LW_FP64) ? 8 : 4;
+  const int Q = p.dim == 2 ? 9 : 19;
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  L.g = take((size_t)Q * n * es);
+  L.c = take(n * es);
+  L.c1 = take(n * es);
+  L.c2 = take(n * es);
+  L.u = take((size_t)p.dim * n * es);
+  L.partials = take(sizeof(double) * lw::kMaxReduceBlocks);
+  L.scalars = take(sizeof(double) * 4);
+  L.status = take(sizeof(unsigned) * 4);
+  L.total = off;
+  return L;
+}
+
+int check_params(const lbm_wenoc_params* p) {
+  if (!p) return LW_EINVAL;
+  if (p->dim != 2 && p->dim != 3) return LW_EINVAL;
+  if (p->nx < 4 || p->ny < 4 || (p->nx % 4) != 0) return LW_EINVAL;
+  if (p->dim == 3 && p->nz < 4) return LW_EINVAL;
+  if (p->dim == 2 && p->ny > 65535) return LW_EINVAL;          // grid.y
+  if (p->dim == 3 && (p->ny > 65535 || p->nz > 65535)) return LW_EINVAL;
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LW_EINVAL;  // stability needs tau > 1/2
+  if (!(p->settling_velocity >= 0.0) || !(p->diffusivity >= 0.0)) return LW_EINVAL;
+  if (!(p->lf_alpha >= 0.0) || !(p->u_cap >= 0.0)) return LW_EINVAL;
+  const double nn = (double)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
+  if (nn > 4.0e9) return LW_EINVAL;
+  return LW_OK;
+}
+
+}  // namespace
+
+struct lbm_wenoc {
+  lbm_wenoc_params p{};
+  Layout L{};
+  unsigned char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool fp64 = false, walls = true, frozen = false, use_graphs = true;
+  long long n = 0;
+  int parity = 0;  // AA-pattern parity of the population array
+  bool initialised = false;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  double alpha = 0.0;
+  // graphs: [parity] -> graph of kGraphSteps steps starting at that parity; and 1 step
+  static constexpr int kGraphSteps = 16;
+  cudaGraphExec_t graph_many[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_one[2] = {nullptr, nullptr};
+  // profiling
+  bool profiling = false;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<std::string> kind_names;
+  std::vector<int64_t> kind_launches;
+  std::vector<double> kind_ms;
+};
+
+namespace {
+
+template <typename T>
+Args<T> make_args(const lbm_wenoc* h) {
+  Args<T> a{};
+  unsigned char* b = h->ws;
+  a.g = reinterpret_cast<T*>(b + h->L.g);
+  a.c = reinterpret_cast<T*>(b + h->L.c);
+  a.c1 = reinterpret_cast<T*>(b + h->L.c1);
+  a.c2 = reinterpret_cast<T*>(b + h->L.c2);
+  a.u = reinterpret_cast<T*>(b + h->L.u);
+  a.partials = reinterpret_cast<double*>(b + h->L.partials);
+  a.scalars = reinterpret_cast<double*>(b + h->L.scalars);
+  a.status = reinterpret_cast<unsigned*>(b + h->L.status);
+  a.ticket = a.status + 1;
+  const lbm_wenoc_params& p = h->p;
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.nz = p.dim == 3 ? p.nz : 1;
+  a.n = h->n;
+  a.walls = h->walls ? 1 : 0;
+  a.omega = T(1.0 / p.tau);
+  a.guo = T(1.0 - 0.5 / p.tau);
+  a.A = T(p.gravity * p.density_contrast);
+  for (int d = 0; d < 3; ++d) a.bf[d] = T(p.body_force[d]);
+  a.vs = T(p.settling_velocity);
+  a.kappa = T(p.diffusivity);
+  a.alpha = T(h->alpha);
+  a.inv_alpha = T(1.0 / h->alpha);
+  a.u_cap = T(p.u_cap);
+  return a;
+}
+
+// Kernel families for timing.
+enum Kind { K_LBM = 0, K_STAGE1, K_STAGE2, K_STAGE3, K_DEPOSIT, K_RK3_SWEEP, K_OTHER, K_COUNT };
+const char* kKindNames[K_COUNT] = {"lbm_collide_stream", "rk_stage1", "rk_stage2", "rk_stage3",
+                                   "deposit_reduce", "rk3_sweep2d", "other"};
+
+cudaEvent_t take_event(lbm_wenoc* h) {
+  if (h->event_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = h->event_pool.back();
+  h->event_pool.pop_back();
+  return e;
+}
+
+void fold_pending(lbm_wenoc* h) {
+  for (auto& pe : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+      h->kind_ms[pe.kind] += ms;
+      h->kind_launches[pe.kind] += 1;
+    }
+    h->event_pool.push_back(pe.a);
+    h->event_pool.push_back(pe.b);
+  }
+  h->pending.clear();
+}
+
+// Wrap one launch: optional event pair, launch counting.
+template <typename F>
+void launch(lbm_wenoc* h, int kind, F&& f) {
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (h->profiling) {
+    if (h->pending.size() >= 4096) {
+      cudaStreamSynchronize(h->stream);
+      fold_pending(h);
+    }
+    ea = take_event(h);
+    eb = take_event(h);
+    if (ea) cudaEventRecord(ea, h->stream);
+  }
+  f();
+  h->launches++;
+  if (ea && eb) {
+    cudaEventRecord(eb, h->stream);
+    h->pending.push_back({kind, ea, eb});
+  }
+}
+
+bool use_sweep(const lbm_wenoc* h) {
+  return !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(h->p.nx, h->p.ny);
+}
+
+template <class LAT, typename T>
+void enqueue_step(lbm_wenoc* h, int parity) {
+  Args<T> a = make_args<T>(h);
+  const dim3 blk(kLbmThreads);
+  const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
+  cudaStream_t s = h->stream;
+  if (!h->frozen) {
+    launch(h, K_LBM, [&] {
+      if (parity == 0)
+        lw::lbm_step_kernel<LAT, T, 0><<<grd, blk, 0, s>>>(a);
+      else
+        lw::lbm_step_kernel<LAT, T, 1><<<grd, blk, 0, s>>>(a);
+    });
+  }
+  const long long nfloor = (long long)a.nx * (LAT::DIM == 3 ? a.ny : 1);
+  const int dep_blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (nfloor + 4095) / 4096);
+  if (std::is_same<T, float>::value && LAT::DIM == 2 && use_sweep(h)) {
+    launch(h, K_RK3_SWEEP, [&] { lw::launch_sweep2d(reinterpret_cast<const Args<float>&>(a), s); });
+    return;
+  }
+  launch(h, K_STAGE1, [&] { lw::rk_stage_kernel<T, LAT::DIM, 1><<<grd, blk, 0, s>>>(a); });
+  launch(h, K_STAGE2, [&] { lw::rk_stage_kernel<T, LAT::DIM, 2><<<grd, blk, 0, s>>>(a); });
+  if (h->walls)
+    launch(h, K_DEPOSIT, [&] {
+      lw::deposit_kernel<T><<<dep_blocks, lw::kReduceThreads, 0, s>>>(a, nfloor);
+    });
+  launch(h, K_STAGE3, [&] { lw::rk_stage_kernel<T, LAT::DIM, 3><<<grd, blk, 0, s>>>(a); });
+}
+
+void enqueue_one(lbm_wenoc* h, int parity) {
+  if (h->p.dim == 2) {
+    if (h->fp64)
+      enqueue_step<D2Q9, double>(h, parity);
+    else
+      enqueue_step<D2Q9, float>(h, parity);
+  } else {
+    if (h->fp64)
+      enqueue_step<D3Q19, double>(h, parity);
+    else
+      enqueue_step<D3Q19, float>(h, parity);
+  }
+}
+
+void destroy_graphs(lbm_wenoc* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->graph_many[i]) cudaGraphExecDestroy(h->graph_many[i]);
+    if (h->graph_one[i]) cudaGraphExecDestroy(h->graph_one[i]);
+    h->graph_many[i] = h->graph_one[i] = nullptr;
+  }
+}
+
+// Capture `count` steps starting at `parity` on a private stream.
+int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LW_ECUDA;
+  cudaStream_t saved = h->stream;
+  const int64_t saved_launches = h->launches;
+  h->stream = cap;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < count; ++k) enqueue_one(h, (parity + k) & 1);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  h->stream = saved;
+  h->launches = saved_launches;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  return e == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+int launches_per_step(const lbm_wenoc* h) {
+  if (!h->fp64 && h->p.dim == 2 && use_sweep(h)) return h->frozen ? 1 : 2;
+  return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0);
+}
+
+int sync_and_status(lbm_wenoc* h) {
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  unsigned st[2] = {0, 0};
+  if (cudaMemcpy(st, h->ws + h->L.status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return LW_ECUDA;
+  if (st[0] & lw::kStatusTimeout) return LW_ETIMEOUT;
+  if (st[0] & lw::kStatusUnstable) return LW_EUNSTABLE;
+  return LW_OK;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class LAT, typename T>
+void launch_fields(lbm_wenoc* h, T* rho, T* u) {
+  Args<T> a = make_args<T>(h);
+  const dim3 blk(kLbmThreads);
+  const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
+  if (h->parity == 0)
+    lw::fields_kernel<LAT, T, 0><<<grd, blk, 0, h->stream>>>(a, rho, u);
+  else
+    lw::fields_kernel<LAT, T, 1><<<grd, blk, 0, h->stream>>>(a, rho, u);
+}
+
+template <class LAT, typename T>
+void launch_init(lbm_wenoc* h, const T* u0) {
+  Args<T> a = make_args<T>(h);
+  const dim3 blk(kLbmThreads);
+  const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
+  lw::init_kernel<LAT, T><<<grd, blk, 0, h->stream>>>(a, u0);
+}
+
+template <typename T>
+__global__ void fill_kernel(T* p, long long n, T v) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < n) p[k] = v;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_wenoc_workspace_bytes(const lbm_wenoc_params* p, size_t* bytes) {
+  if (!bytes) return LW_EINVAL;
+  int rc = check_params(p);
+  if (rc != LW_OK) return rc;
+  *bytes = make_layout(*p).total;
+  return LW_OK;
+}
+
+int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t bytes, void* cuda_stream,
+                     lbm_wenoc** out) {
+  if (!out) return LW_EINVAL;
+  *out = nullptr;
+  int rc = check_params(p);
+  if (rc != LW_OK) return rc;
+  if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255u) != 0) return LW_EINVAL;
+  Layout L = make_layout(*p);
+  if (bytes < L.total) return LW_ENOMEM;
+  lbm_wenoc* h = new (std::nothrow) lbm_wenoc();
+  if (!h) return LW_ENOMEM;
+  h->p = *p;
+  if (h->p.dim == 2) h->p.nz = 1;
+  if (h->p.u_cap <= 0.0) h->p.u_cap = 0.1;
+  h->L = L;
+  h->ws = static_cast<unsigned char*>(dev_workspace);
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->fp64 = (p->flags & LW_FP64) != 0;
+  h->walls = (p->flags & LW_PERIODIC_VERTICAL) == 0;
+  h->frozen = (p->flags & LW_FROZEN_VELOCITY) != 0;
+  h->use_graphs = (p->flags & LW_NO_GRAPH) == 0;
+  h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
+  h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : p->settling_velocity + h->p.u_cap;
+  cudaGetDevice(&h->device);
+  h->kind_names.assign(kKindNames, kKindNames + K_COUNT);
+  h->kind_launches.assign(K_COUNT, 0);
+  h->kind_ms.assign(K_COUNT, 0.0);
+  *out = h;
+  return LW_OK;
+}
+
+int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
+  if (!h || !c0) return LW_EINVAL;
+  const size_t es = h->fp64 ? 8 : 4;
+  const size_t cbytes = (size_t)h->n * es;
+  const size_t ubytes = cbytes * h->p.dim;
+  // c0 -> c buffer (device or host source); u0 -> c1 scratch first (init reads it)
+  cudaMemcpyKind kc = is_device_pointer(c0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(h->ws + h->L.c, c0, cbytes, kc, h->stream) != cudaSuccess) return LW_ECUDA;
+  const void* u0dev = nullptr;
+  if (u0) {
+    cudaMemcpyKind ku = is_device_pointer(u0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // stage through the population buffer's tail is unsafe; use u itself then copy in kernel
+    if (cudaMemcpyAsync(h->ws + h->L.u, u0, ubytes, ku, h->stream) != cudaSuccess) return LW_ECUDA;
+    u0dev = h->ws + h->L.u;
+  }
+  if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (h->p.dim == 2) {
+    if (h->fp64)
+      launch_init<D2Q9, double>(h, static_cast<const double*>(u0dev));
+    else
+      launch_init<D2Q9, float>(h, static_cast<const float*>(u0dev));
+  } else {
+    if (h->fp64)
+      launch_init<D3Q19, double>(h, static_cast<const double*>(u0dev));
+    else
+      launch_init<D3Q19, float>(h, static_cast<const float*>(u0dev));
+  }
+  if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
+  // host sources may be pageable: make the call safe to return
+  if (kc == cudaMemcpyHostToDevice || (u0 && !is_device_pointer(u0)))
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  h->parity = 0;
+  h->steps = 0;
+  h->initialised = true;
+  return LW_OK;
+}
+
+int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const int per_step = launches_per_step(h);
+  int64_t left = nsteps;
+  if (h->use_graphs && !h->profiling) {
+    while (left > 0) {
+      const int par = h->frozen ? 0 : h->parity;
+      cudaGraphExec_t* slot;
+      int count;
+      if (left >= lbm_wenoc::kGraphSteps) {
+        slot = &h->graph_many[par];
+        count = lbm_wenoc::kGraphSteps;
+      } else {
+        slot = &h->graph_one[par];
+        count = 1;
+      }
+      if (!*slot) {
+        int rc = capture_graph(h, par, count, slot);
+        if (rc != LW_OK) return rc;
+      }
+      if (cudaGraphLaunch(*slot, h->stream) != cudaSuccess) return LW_ECUDA;
+      h->launches += (int64_t)per_step * count;
+      if (!h->frozen) h->parity = (h->parity + count) & 1;
+      h->steps += count;
+      left -= count;
+    }
+  } else {
+    for (; left > 0; --left) {
+      enqueue_one(h, h->frozen ? 0 : h->parity);
+      if (!h->frozen) h->parity ^= 1;
+      h->steps += 1;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
+  return LW_OK;
+}
+
+int lbm_wenoc_deposited_mass(lbm_wenoc* h, double* out) {
+  if (!h || !out) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  int rc = sync_and_status(h);
+  if (rc == LW_ECUDA) return rc;
+  if (cudaMemcpy(out, h->ws + h->L.scalars, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LW_ECUDA;
+  return rc;
+}
+
+int lbm_wenoc_total_mass(lbm_wenoc* h, double* out) {
+  if (!h || !out) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const int blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (h->n + 8191) / 8192);
+  if (h->fp64) {
+    Args<double> a = make_args<double>(h);
+    lw::sum_kernel<double><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, a.c, h->n);
+  } else {
+    Args<float> a = make_args<float>(h);
+    lw::sum_kernel<float><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, a.c, h->n);
+  }
+  if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemcpy(out, h->ws + h->L.scalars + sizeof(double), sizeof(double), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return LW_ECUDA;
+  return LW_OK;
+}
+
+int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
+  if (!h) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const size_t es = h->fp64 ? 8 : 4;
+  const size_t cbytes = (size_t)h->n * es;
+  // Compute rho and u into the stage buffers (free between steps), then copy out.
+  unsigned char* rho_dev = h->ws + h->L.c1;
+  unsigned char* u_dev = h->ws + h->L.u;
+  if (rho || u) {
+    if (h->frozen) {
+      const int blocks = (int)((h->n + 255) / 256);
+      if (h->fp64)
+        fill_kernel<double><<<blocks, 256, 0, h->stream>>>(reinterpret_cast<double*>(rho_dev), h->n, 1.0);
+      else
+        fill_kernel<float><<<blocks, 256, 0, h->stream>>>(reinterpret_cast<float*>(rho_dev), h->n, 1.0f);
+    } else {
+      // The velocity buffer is scratch between steps (rewritten by the next step), so
+      // the fields kernel may overwrite it with the velocity of the current state.
+      if (h->p.dim == 2) {
+        if (h->fp64)
+          launch_fields<D2Q9, double>(h, reinterpret_cast<double*>(rho_dev), reinterpret_cast<double*>(u_dev));
+        else
+          launch_fields<D2Q9, float>(h, reinterpret_cast<float*>(rho_dev), reinterpret_cast<float*>(u_dev));
+      } else {
+        if (h->fp64)
+          launch_fields<D3Q19, double>(h, reinterpret_cast<double*>(rho_dev), reinterpret_cast<double*>(u_dev));
+        else
+          launch_fields<D3Q19, float>(h, reinterpret_cast<float*>(rho_dev), reinterpret_cast<float*>(u_dev));
+      }
+    }
+    if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
+  }
+  auto copy_out = [&](void* dst, const void* src, size_t nbytes) -> bool {
+    cudaMemcpyKind k = is_device_pointer(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    return cudaMemcpyAsync(dst, src, nbytes, k, h->stream) == cudaSuccess;
+  };
+  if (rho && !copy_out(rho, rho_dev, cbytes)) return LW_ECUDA;
+  if (u && !copy_out(u, u_dev, cbytes * h->p.dim)) return LW_ECUDA;
+  if (c && !copy_out(c, h->ws + h->L.c, cbytes)) return LW_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  return LW_OK;
+}
+
+int lbm_wenoc_status(lbm_wenoc* h) {
+  if (!h) return LW_EINVAL;
+  return sync_and_status(h);
+}
+
+int64_t lbm_wenoc_steps(const lbm_wenoc* h) { return h ? h->steps : -1; }
+
+int64_t lbm_wenoc_launch_count(const lbm_wenoc* h) { return h ? h->launches : -1; }
+
+int lbm_wenoc_profile_enable(lbm_wenoc* h, int enable) {
+  if (!h) return LW_EINVAL;
+  h->profiling = enable != 0;
+  return LW_OK;
+}
+
+int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, int* count, int reset) {
+  if (!h || !count) return LW_EINVAL;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  fold_pending(h);
+  int k = 0;
+  for (int i = 0; i < K_COUNT; ++i) {
+    if (h->kind_launches[i] == 0) continue;
+    if (out && k < max) {
+      std::memset(out[k].name, 0, sizeof(out[k].name));
+      std::strncpy(out[k].name, h->kind_names[i].c_str(), sizeof(out[k].name) - 1);
+      out[k].launches = h->kind_launches[i];
+      out[k].total_ms = h->kind_ms[i];
+    }
+    ++k;
+  }
+  *count = k;
+  if (reset) {
+    std::fill(h->kind_launches.begin(), h->kind_launches.end(), 0);
+    std::fill(h->kind_ms.begin(), h->kind_ms.end(), 0.0);
+  }
+  return LW_OK;
+}
+
+void lbm_wenoc_destroy(lbm_wenoc* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  fold_pending(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  destroy_graphs(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+"""Python binding of the lbm_wenoc C ABI (include/lbm_wenoc.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+liblbm_wenoc.so.  There is no CPU fallback -- if the library is not built, or no
+CUDA device is present, the calls raise.
+
+The functions carry the C names; ``Simulation`` is a convenience wrapper that
+allocates the workspace with PyTorch on the current device and passes torch's
+current stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+LW_OK = 0
+LW_EINVAL = -1
+LW_ENOMEM = -2
+LW_ECUDA = -3
+LW_EUNSTABLE = -4
+LW_ETIMEOUT = -5
+LW_ESTATE = -6
+
+LW_FP64 = 0x1
+LW_PERIODIC_VERTICAL = 0x2
+LW_FROZEN_VELOCITY = 0x4
+LW_NO_GRAPH = 0x8
+
+_ERRORS = {LW_EINVAL: "LW_EINVAL", LW_ENOMEM: "LW_ENOMEM", LW_ECUDA: "LW_ECUDA",
+           LW_EUNSTABLE: "LW_EUNSTABLE", LW_ETIMEOUT: "LW_ETIMEOUT", LW_ESTATE: "LW_ESTATE"}
+
+EXPORTED = [
+    "lbm_wenoc_workspace_bytes", "lbm_wenoc_create", "lbm_wenoc_init", "lbm_wenoc_step",
+    "lbm_wenoc_deposited_mass", "lbm_wenoc_total_mass", "lbm_wenoc_fields", "lbm_wenoc_status",
+    "lbm_wenoc_steps", "lbm_wenoc_profile_enable", "lbm_wenoc_profile_read",
+    "lbm_wenoc_launch_count", "lbm_wenoc_destroy",
+]
+
+
+class LbmWenocError(RuntimeError):
+    def __init__(self, call, code):
+        super().__init__(f"{call} returned {_ERRORS.get(code, code)}")
+        self.code = code
+
+
+class lbm_wenoc_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("gravity", ctypes.c_double),
+        ("density_contrast", ctypes.c_double),
+        ("settling_velocity", ctypes.c_double),
+        ("diffusivity", ctypes.c_double),
+        ("lf_alpha", ctypes.c_double),
+        ("u_cap", ctypes.c_double),
+        ("body_force", ctypes.c_double * 3),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class lbm_wenoc_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblbm_wenoc.so")
+
+
+def load():
+    """Load liblbm_wenoc.so (built by paper_2106_07694_gb300.build.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    P = ctypes.POINTER(lbm_wenoc_params)
+    L.lbm_wenoc_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm_wenoc_create.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.lbm_wenoc_init.argtypes = [vp, vp, vp]
+    L.lbm_wenoc_step.argtypes = [vp, i64]
+    L.lbm_wenoc_deposited_mass.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.lbm_wenoc_total_mass.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.lbm_wenoc_fields.argtypes = [vp, vp, vp, vp]
+    L.lbm_wenoc_status.argtypes = [vp]
+    L.lbm_wenoc_steps.argtypes = [vp]
+    L.lbm_wenoc_steps.restype = i64
+    L.lbm_wenoc_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.lbm_wenoc_profile_read.argtypes = [vp, ctypes.POINTER(lbm_wenoc_kernel_stat), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.lbm_wenoc_launch_count.argtypes = [vp]
+    L.lbm_wenoc_launch_count.restype = i64
+    L.lbm_wenoc_destroy.argtypes = [vp]
+    L.lbm_wenoc_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("lbm_wenoc_steps", "lbm_wenoc_launch_count", "lbm_wenoc_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(call, rc):
+    if rc != LW_OK:
+        raise LbmWenocError(call, rc)
+    return rc
+
+
+def _ptr(x):
+    """Address of a torch tensor, a numpy array or an int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+# ---- the C entry points, same names --------------------------------------------------
+
+def lbm_wenoc_workspace_bytes(params):
+    n = ctypes.c_size_t(0)
+    _check("lbm_wenoc_workspace_bytes", load().lbm_wenoc_workspace_bytes(ctypes.byref(params), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_wenoc_create(params, workspace, nbytes, stream):
+    h = ctypes.c_void_p()
+    _check("lbm_wenoc_create", load().lbm_wenoc_create(ctypes.byref(params), _ptr(workspace), nbytes,
+                                                       stream, ctypes.byref(h)))
+    return h
+
+
+def lbm_wenoc_init(h, c0, u0=None):
+    return _check("lbm_wenoc_init", load().lbm_wenoc_init(h, _ptr(c0), _ptr(u0)))
+
+
+def lbm_wenoc_step(h, nsteps):
+    return _check("lbm_wenoc_step", load().lbm_wenoc_step(h, int(nsteps)))
+
+
+def lbm_wenoc_deposited_mass(h):
+    out = ctypes.c_double()
+    _check("lbm_wenoc_deposited_mass", load().lbm_wenoc_deposited_mass(h, ctypes.byref(out)))
+    return out.value
+
+
+def lbm_wenoc_total_mass(h):
+    out = ctypes.c_double()
+    _check("lbm_wenoc_total_mass", load().lbm_wenoc_total_mass(h, ctypes.byref(out)))
+    return out.value
+
+
+def lbm_wenoc_fields(h, rho=None, u=None, c=None):
+    return _check("lbm_wenoc_fields", load().lbm_wenoc_fields(h, _ptr(rho), _ptr(u), _ptr(c)))
+
+
+def lbm_wenoc_status(h):
+    return load().lbm_wenoc_status(h)
+
+
+def lbm_wenoc_steps(h):
+    return load().lbm_wenoc_steps(h)
+
+
+def lbm_wenoc_launch_count(h):
+    return load().lbm_wenoc_launch_count(h)
+
+
+def lbm_wenoc_profile_enable(h, enable=True):
+    return _check("lbm_wenoc_profile_enable", load().lbm_wenoc_profile_enable(h, 1 if enable else 0))
+
+
+def lbm_wenoc_profile_read(h, reset=False):
+    stats = (lbm_wenoc_kernel_stat * 16)()
+    count = ctypes.c_int(0)
+    _check("lbm_wenoc_profile_read", load().lbm_wenoc_profile_read(h, stats, 16, ctypes.byref(count),
+                                                                   1 if reset else 0))
+    return {stats[i].name.decode(): (stats[i].launches, stats[i].total_ms) for i in range(count.value)}
+
+
+def lbm_wenoc_destroy(h):
+    if h:
+        load().lbm_wenoc_destroy(h)
+
+
+# ---- convenience wrapper ---------------------------------------------------------------
+
+def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0,
+                diffusivity=0.0, lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), fp64=False,
+                periodic_vertical=False, frozen_velocity=False, graphs=True):
+    p = lbm_wenoc_params()
+    p.dim = len(shape)
+    p.nx, p.ny = int(shape[0]), int(shape[1])
+    p.nz = int(shape[2]) if p.dim == 3 else 1
+    p.tau, p.gravity, p.density_contrast = tau, gravity, density_contrast
+    p.settling_velocity, p.diffusivity, p.lf_alpha, p.u_cap = settling_velocity, diffusivity, lf_alpha, u_cap
+    for d in range(3):
+        p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
+    p.flags = ((LW_FP64 if fp64 else 0) | (LW_PERIODIC_VERTICAL if periodic_vertical else 0) |
+               (LW_FROZEN_VELOCITY if frozen_velocity else 0) | (0 if graphs else LW_NO_GRAPH))
+    return p
+
+
+class Simulation:
+    """One handle plus its torch-allocated workspace on the current CUDA device.
+
+    shape = (nx, ny) or (nx, ny, nz); fields are indexed [z][y][x] (vertical slowest).
+    """
+
+    def __init__(self, shape, stream=None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbm_wenoc needs a CUDA device; there is no CPU fallback")
+        load()
+        self.params = make_params(shape, **kw)
+        self.dim = len(shape)
+        self.grid = tuple(reversed([int(s) for s in shape]))
+        self.fp64 = bool(self.params.flags & LW_FP64)
+        self.dtype = torch.float64 if self.fp64 else torch.float32
+        nbytes = lbm_wenoc_workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = lbm_wenoc_create(self.params, self.workspace, nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_wenoc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _as_input(self, a, shape):
+        import torch
+        if isinstance(a, torch.Tensor):
+            t = a.to(self.dtype).contiguous()
+        else:
+            t = torch.as_tensor(np.ascontiguousarray(a), dtype=self.dtype)
+        assert tuple(t.shape) == shape or t.numel() == int(np.prod(shape)), (t.shape, shape)
+        return t
+
+    def init(self, c0, u0=None):
+        c = self._as_input(c0, self.grid)
+        u = None if u0 is None else self._as_input(u0, (self.dim,) + self.grid)
+        self._keep = (c, u)  # host or device sources stay alive across the async copy
+        lbm_wenoc_init(self.handle, c, u)
+
+    def step(self, n=1):
+        lbm_wenoc_step(self.handle, n)
+
+    def fields(self, device="cpu"):
+        import torch
+        rho = torch.empty(self.grid, dtype=self.dtype, device=device)
+        u = torch.empty((self.dim,) + self.grid, dtype=self.dtype, device=device)
+        c = torch.empty(self.grid, dtype=self.dtype, device=device)
+        lbm_wenoc_fields(self.handle, rho, u, c)
+        return rho, u, c
+
+    @property
+    def deposit(self):
+        return lbm_wenoc_deposited_mass(self.handle)
+
+    @property
+    def total_mass(self):
+        return lbm_wenoc_total_mass(self.handle)
+
+    @property
+    def steps(self):
+        return lbm_wenoc_steps(self.handle)
+
+    def status(self):
+        return lbm_wenoc_status(self.handle)
