@@ -128,6 +128,11 @@ int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, in
 /* Number of kernel launches this handle has issued since create. */
 int64_t lbm_wenoc_launch_count(const lbm_wenoc* h);
 
+/* Tuning of the fused 2D FP32 transport kernel: rows per CTA segment (0 = default,
+ * about two CTAs per SM in one wave).  Results do not depend on it (bitwise).  No
+ * effect on other paths.  Drops captured graphs; call between steps. */
+int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows);
+
 /* Destroy the handle (graphs, events).  Does not free the caller's workspace. */
 void lbm_wenoc_destroy(lbm_wenoc* h);
 

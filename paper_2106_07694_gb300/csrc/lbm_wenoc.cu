@@ -101,14 +101,17 @@ struct lbm_wenoc {
   bool fp64 = false, walls = true, frozen = false, use_graphs = true;
   long long n = 0;
   int parity = 0;  // AA-pattern parity of the population array
+  int cur = 0;     // which buffer holds c^n: 0 = c, 1 = c1 (2D FP32 sweep path ping-pongs)
+  bool sweep = false;
+  lw::SweepLaunch sweep_geom{};
   bool initialised = false;
   int64_t steps = 0;
   int64_t launches = 0;
   double alpha = 0.0;
-  // graphs: [parity] -> graph of kGraphSteps steps starting at that parity; and 1 step
+  // graphs keyed by (AA parity, c buffer) at their first step: kGraphSteps steps, and 1 step
   static constexpr int kGraphSteps = 16;
-  cudaGraphExec_t graph_many[2] = {nullptr, nullptr};
-  cudaGraphExec_t graph_one[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_many[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_one[4] = {nullptr, nullptr, nullptr, nullptr};
   // profiling
   bool profiling = false;
   struct Pending {
@@ -129,7 +132,7 @@ Args<T> make_args(const lbm_wenoc* h) {
   Args<T> a{};
   unsigned char* b = h->ws;
   a.g = reinterpret_cast<T*>(b + h->L.g);
-  a.c = reinterpret_cast<T*>(b + h->L.c);
+  a.c = reinterpret_cast<T*>(b + (h->cur ? h->L.c1 : h->L.c));
   a.c1 = reinterpret_cast<T*>(b + h->L.c1);
   a.c2 = reinterpret_cast<T*>(b + h->L.c2);
   a.u = reinterpret_cast<T*>(b + h->L.u);
@@ -205,10 +208,6 @@ void launch(lbm_wenoc* h, int kind, F&& f) {
   }
 }
 
-bool use_sweep(const lbm_wenoc* h) {
-  return !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(h->p.nx, h->p.ny);
-}
-
 template <class LAT, typename T>
 void enqueue_step(lbm_wenoc* h, int parity) {
   Args<T> a = make_args<T>(h);
@@ -225,8 +224,11 @@ void enqueue_step(lbm_wenoc* h, int parity) {
   }
   const long long nfloor = (long long)a.nx * (LAT::DIM == 3 ? a.ny : 1);
   const int dep_blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (nfloor + 4095) / 4096);
-  if (std::is_same<T, float>::value && LAT::DIM == 2 && use_sweep(h)) {
-    launch(h, K_RK3_SWEEP, [&] { lw::launch_sweep2d(reinterpret_cast<const Args<float>&>(a), s); });
+  if (std::is_same<T, float>::value && LAT::DIM == 2 && h->sweep) {
+    const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
+    float* c_out = reinterpret_cast<float*>(h->ws + (h->cur ? h->L.c : h->L.c1));
+    launch(h, K_RK3_SWEEP, [&] { lw::launch_sweep2d(af, c_out, h->sweep_geom, s); });
+    h->cur ^= 1;
     return;
   }
   launch(h, K_STAGE1, [&] { lw::rk_stage_kernel<T, LAT::DIM, 1><<<grd, blk, 0, s>>>(a); });
@@ -253,7 +255,7 @@ void enqueue_one(lbm_wenoc* h, int parity) {
 }
 
 void destroy_graphs(lbm_wenoc* h) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (h->graph_many[i]) cudaGraphExecDestroy(h->graph_many[i]);
     if (h->graph_one[i]) cudaGraphExecDestroy(h->graph_one[i]);
     h->graph_many[i] = h->graph_one[i] = nullptr;
@@ -266,6 +268,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LW_ECUDA;
   cudaStream_t saved = h->stream;
   const int64_t saved_launches = h->launches;
+  const int saved_cur = h->cur;
   h->stream = cap;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -275,6 +278,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
   }
   h->stream = saved;
   h->launches = saved_launches;
+  h->cur = saved_cur;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cap);
@@ -282,7 +286,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
 }
 
 int launches_per_step(const lbm_wenoc* h) {
-  if (!h->fp64 && h->p.dim == 2 && use_sweep(h)) return h->frozen ? 1 : 2;
+  if (h->sweep) return h->frozen ? 1 : 2;
   return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0);
 }
 
@@ -365,6 +369,17 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : p->settling_velocity + h->p.u_cap;
   cudaGetDevice(&h->device);
+  h->sweep = !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls);
+  if (h->sweep) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
+    h->sweep_geom = lw::sweep2d_geometry(p->nx, p->ny, sms, 0);
+    if (cudaFuncSetAttribute(lw::rk3_sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lw::sweep2d_smem()) != cudaSuccess) {
+      delete h;
+      return LW_ECUDA;
+    }
+  }
   h->kind_names.assign(kKindNames, kKindNames + K_COUNT);
   h->kind_launches.assign(K_COUNT, 0);
   h->kind_ms.assign(K_COUNT, 0.0);
@@ -374,6 +389,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
 
 int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
   if (!h || !c0) return LW_EINVAL;
+  h->cur = 0;
   const size_t es = h->fp64 ? 8 : 4;
   const size_t cbytes = (size_t)h->n * es;
   const size_t ubytes = cbytes * h->p.dim;
@@ -405,6 +421,7 @@ int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
   if (kc == cudaMemcpyHostToDevice || (u0 && !is_device_pointer(u0)))
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
   h->parity = 0;
+  h->cur = 0;
   h->steps = 0;
   h->initialised = true;
   return LW_OK;
@@ -418,13 +435,14 @@ int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
   if (h->use_graphs && !h->profiling) {
     while (left > 0) {
       const int par = h->frozen ? 0 : h->parity;
+      const int key = par * 2 + h->cur;
       cudaGraphExec_t* slot;
       int count;
       if (left >= lbm_wenoc::kGraphSteps) {
-        slot = &h->graph_many[par];
+        slot = &h->graph_many[key];
         count = lbm_wenoc::kGraphSteps;
       } else {
-        slot = &h->graph_one[par];
+        slot = &h->graph_one[key];
         count = 1;
       }
       if (!*slot) {
@@ -434,6 +452,7 @@ int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
       if (cudaGraphLaunch(*slot, h->stream) != cudaSuccess) return LW_ECUDA;
       h->launches += (int64_t)per_step * count;
       if (!h->frozen) h->parity = (h->parity + count) & 1;
+      if (h->sweep) h->cur = (h->cur + count) & 1;
       h->steps += count;
       left -= count;
     }
@@ -483,7 +502,7 @@ int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
   const size_t es = h->fp64 ? 8 : 4;
   const size_t cbytes = (size_t)h->n * es;
   // Compute rho and u into the stage buffers (free between steps), then copy out.
-  unsigned char* rho_dev = h->ws + h->L.c1;
+  unsigned char* rho_dev = h->ws + h->L.c2;  // free between steps on every path
   unsigned char* u_dev = h->ws + h->L.u;
   if (rho || u) {
     if (h->frozen) {
@@ -515,7 +534,7 @@ int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
   };
   if (rho && !copy_out(rho, rho_dev, cbytes)) return LW_ECUDA;
   if (u && !copy_out(u, u_dev, cbytes * h->p.dim)) return LW_ECUDA;
-  if (c && !copy_out(c, h->ws + h->L.c, cbytes)) return LW_ECUDA;
+  if (c && !copy_out(c, h->ws + (h->cur ? h->L.c1 : h->L.c), cbytes)) return LW_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
   return LW_OK;
 }
@@ -555,6 +574,17 @@ int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, in
     std::fill(h->kind_launches.begin(), h->kind_launches.end(), 0);
     std::fill(h->kind_ms.begin(), h->kind_ms.end(), 0.0);
   }
+  return LW_OK;
+}
+
+int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows) {
+  if (!h || rows < 0) return LW_EINVAL;
+  if (!h->sweep) return LW_OK;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  destroy_graphs(h);
+  h->sweep_geom = lw::sweep2d_geometry(h->p.nx, h->p.ny, sms, rows);
   return LW_OK;
 }
 

@@ -33,7 +33,7 @@ EXPORTED = [
     "lbm_wenoc_workspace_bytes", "lbm_wenoc_create", "lbm_wenoc_init", "lbm_wenoc_step",
     "lbm_wenoc_deposited_mass", "lbm_wenoc_total_mass", "lbm_wenoc_fields", "lbm_wenoc_status",
     "lbm_wenoc_steps", "lbm_wenoc_profile_enable", "lbm_wenoc_profile_read",
-    "lbm_wenoc_launch_count", "lbm_wenoc_destroy",
+    "lbm_wenoc_launch_count", "lbm_wenoc_set_segment_rows", "lbm_wenoc_destroy",
 ]
 
 
@@ -98,6 +98,7 @@ def load():
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.lbm_wenoc_launch_count.argtypes = [vp]
     L.lbm_wenoc_launch_count.restype = i64
+    L.lbm_wenoc_set_segment_rows.argtypes = [vp, ctypes.c_int32]
     L.lbm_wenoc_destroy.argtypes = [vp]
     L.lbm_wenoc_destroy.restype = None
     for name in EXPORTED:
@@ -185,6 +186,10 @@ def lbm_wenoc_profile_read(h, reset=False):
     _check("lbm_wenoc_profile_read", load().lbm_wenoc_profile_read(h, stats, 16, ctypes.byref(count),
                                                                    1 if reset else 0))
     return {stats[i].name.decode(): (stats[i].launches, stats[i].total_ms) for i in range(count.value)}
+
+
+def lbm_wenoc_set_segment_rows(h, rows):
+    return _check("lbm_wenoc_set_segment_rows", load().lbm_wenoc_set_segment_rows(h, int(rows)))
 
 
 def lbm_wenoc_destroy(h):
