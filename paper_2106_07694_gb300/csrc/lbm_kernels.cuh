@@ -140,6 +140,81 @@ __global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
   }
 }
 
+// D2Q9 specialisation of the fused collide-stream (same arithmetic as lbm_step_kernel):
+// 32-bit node offsets, the three source rows and columns hoisted, the wall test of
+// a row taken once per block (a block is one row segment), and streaming cache
+// hints on the population traffic (each population is touched once per step), so
+// that c and u stay in L2 for the transport kernel that follows.
+template <typename T, int PARITY>
+__global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (x >= nx) return;
+  const unsigned n = (unsigned)a.n;
+  const unsigned node = (unsigned)y * (unsigned)nx + (unsigned)x;
+  const bool walls = a.walls != 0;
+  // neighbour offsets relative to node along x and y (periodic x; y periodic or walled)
+  const int dxm = x == 0 ? nx - 1 : -1;          // offset of x-1
+  const int dxp = x == nx - 1 ? -(nx - 1) : 1;   // offset of x+1
+  const bool bot = y == 0, top = y == ny - 1;
+  const int dym = bot ? (walls ? 0 : (ny - 1) * nx) : -nx;  // offset of y-1 (0: wall)
+  const int dyp = top ? (walls ? 0 : -(ny - 1) * nx) : nx;  // offset of y+1 (0: wall)
+  const bool wall_m = walls && bot, wall_p = walls && top;
+  T* __restrict__ G = a.g;
+  auto off = [&](int i, int s) -> int {  // offset of node + s*c_i (s = +-1), without the wall test
+    const int cx = s * D2Q9::cx(i), cy = s * D2Q9::cy(i);
+    return (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) + (cy > 0 ? dyp : (cy < 0 ? dym : 0));
+  };
+  auto behind_wall = [&](int i, int s) -> bool {
+    const int cy = s * D2Q9::cy(i);
+    return (cy < 0 && wall_m) || (cy > 0 && wall_p);
+  };
+
+  T g[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    if (PARITY == 0) {
+      g[i] = __ldcs(G + i * n + node);
+    } else {
+      g[i] = behind_wall(i, -1) ? __ldcs(G + i * n + node)
+                                : __ldcs(G + D2Q9::opp(i) * n + (unsigned)((int)node + off(i, -1)));
+    }
+  }
+  T drho = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    drho += g[i];
+    if (D2Q9::cx(i)) jx += D2Q9::cx(i) * g[i];
+    if (D2Q9::cy(i)) jy += D2Q9::cy(i) * g[i];
+  }
+  const T Fx = a.bf[0], Fy = a.bf[1] - a.A * a.c[node];
+  const T rho = T(1) + drho;
+  const T inv_rho = T(1) / rho;
+  const T ux = (jx + T(0.5) * Fx) * inv_rho, uy = (jy + T(0.5) * Fy) * inv_rho;
+  a.u[node] = ux;
+  a.u[n + node] = uy;
+  report_status(a.status, !finite_val(rho) || !(fabs(ux) <= a.u_cap) || !(fabs(uy) <= a.u_cap));
+  const T uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T wi = T(D2Q9::w(i));
+    const T cu = D2Q9::cx(i) * ux + D2Q9::cy(i) * uy;
+    const T cF = D2Q9::cx(i) * Fx + D2Q9::cy(i) * Fy;
+    const T geq = wi * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    const T src = a.guo * wi * (T(3) * (cF - uF) + T(9) * cu * cF);
+    const T gs = g[i] - a.omega * (g[i] - geq) + src;
+    if (PARITY == 0) {
+      __stcs(G + D2Q9::opp(i) * n + node, gs);
+    } else {
+      if (behind_wall(i, +1))
+        __stcs(G + D2Q9::opp(i) * n + node, gs);
+      else
+        __stcs(G + i * n + (unsigned)((int)node + off(i, +1)), gs);
+    }
+  }
+}
+
 // Macroscopic fields of the current state (parity as in load_populations):
 // rho, u = (sum g c + F/2)/rho with the current c.
 template <class LAT, typename T, int PARITY>

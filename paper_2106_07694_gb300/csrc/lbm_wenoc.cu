@@ -216,10 +216,17 @@ void enqueue_step(lbm_wenoc* h, int parity) {
   cudaStream_t s = h->stream;
   if (!h->frozen) {
     launch(h, K_LBM, [&] {
-      if (parity == 0)
-        lw::lbm_step_kernel<LAT, T, 0><<<grd, blk, 0, s>>>(a);
-      else
-        lw::lbm_step_kernel<LAT, T, 1><<<grd, blk, 0, s>>>(a);
+      if (LAT::DIM == 2) {
+        if (parity == 0)
+          lw::lbm_d2q9_kernel<T, 0><<<grd, blk, 0, s>>>(a);
+        else
+          lw::lbm_d2q9_kernel<T, 1><<<grd, blk, 0, s>>>(a);
+      } else {
+        if (parity == 0)
+          lw::lbm_step_kernel<LAT, T, 0><<<grd, blk, 0, s>>>(a);
+        else
+          lw::lbm_step_kernel<LAT, T, 1><<<grd, blk, 0, s>>>(a);
+      }
     });
   }
   const long long nfloor = (long long)a.nx * (LAT::DIM == 3 ? a.ny : 1);
