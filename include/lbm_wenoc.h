@@ -133,6 +133,22 @@ int64_t lbm_wenoc_launch_count(const lbm_wenoc* h);
  * effect on other paths.  Drops captured graphs; call between steps. */
 int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows);
 
+/* Sum of a concentration field, FP64, for callers that cannot allocate device memory
+ * (an application that owns a fixed device arena, a plugin inside another framework's
+ * allocator, a tool holding only a pointer to someone else's field).  The paper has no
+ * counterpart: this is a service of the library, the same reduction as
+ * lbm_wenoc_total_mass() without a handle or workspace.
+ *   c_dev    device array of n concentrations (double if fp64 != 0, else float)
+ *   n        1 .. 67,108,864 (2048 blocks x 32768 elements); larger -> LW_EINVAL
+ *   out_dev  device address of one double that receives the sum
+ * Asynchronous on cuda_stream.  The partial sums live in a 16 KB static device array
+ * that every GPU loading the library keeps until exit; no cudaMalloc or cudaFree is
+ * called.  The first call on each device looks up that array's address, so make it
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be ordered by the caller. */
+int lbm_wenoc_total_mass_noalloc(const void* c_dev, int64_t n, int32_t fp64, void* cuda_stream,
+                                 double* out_dev);
+
 /* Destroy the handle (graphs, events).  Does not free the caller's workspace. */
 void lbm_wenoc_destroy(lbm_wenoc* h);
 

@@ -44,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if all(os.path.getmtime(s) <= t for s in _sources()):
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + NVCC_FLAGS + ["-I" + INCLUDE, "-o", tmp, os.path.join(CSRC, "lbm_wenoc.cu")]
+    cmd = [nvcc()] + NVCC_FLAGS + ["-I" + INCLUDE, "-o", tmp, os.path.join(CSRC, "lbm_wenoc.cu"),
+                                   os.path.join(CSRC, "noalloc.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

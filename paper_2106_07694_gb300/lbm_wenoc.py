@@ -33,7 +33,8 @@ EXPORTED = [
     "lbm_wenoc_workspace_bytes", "lbm_wenoc_create", "lbm_wenoc_init", "lbm_wenoc_step",
     "lbm_wenoc_deposited_mass", "lbm_wenoc_total_mass", "lbm_wenoc_fields", "lbm_wenoc_status",
     "lbm_wenoc_steps", "lbm_wenoc_profile_enable", "lbm_wenoc_profile_read",
-    "lbm_wenoc_launch_count", "lbm_wenoc_set_segment_rows", "lbm_wenoc_destroy",
+    "lbm_wenoc_launch_count", "lbm_wenoc_set_segment_rows", "lbm_wenoc_total_mass_noalloc",
+    "lbm_wenoc_destroy",
 ]
 
 
@@ -99,6 +100,7 @@ def load():
     L.lbm_wenoc_launch_count.argtypes = [vp]
     L.lbm_wenoc_launch_count.restype = i64
     L.lbm_wenoc_set_segment_rows.argtypes = [vp, ctypes.c_int32]
+    L.lbm_wenoc_total_mass_noalloc.argtypes = [vp, i64, ctypes.c_int32, vp, vp]
     L.lbm_wenoc_destroy.argtypes = [vp]
     L.lbm_wenoc_destroy.restype = None
     for name in EXPORTED:
@@ -190,6 +192,13 @@ def lbm_wenoc_profile_read(h, reset=False):
 
 def lbm_wenoc_set_segment_rows(h, rows):
     return _check("lbm_wenoc_set_segment_rows", load().lbm_wenoc_set_segment_rows(h, int(rows)))
+
+
+def lbm_wenoc_total_mass_noalloc(c_dev, n, fp64, stream, out_dev):
+    """Sum of n concentrations at c_dev into the double at out_dev, with no device
+    allocation (scratch in a fixed static device array; see the C header)."""
+    return _check("lbm_wenoc_total_mass_noalloc",
+                  load().lbm_wenoc_total_mass_noalloc(_ptr(c_dev), int(n), 1 if fp64 else 0, stream, _ptr(out_dev)))
 
 
 def lbm_wenoc_destroy(h):
