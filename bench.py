@@ -97,6 +97,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# captures summarised in profiles/, with the SHA-1 prefix of the kernel source they were
+# taken on; a changed kernel reports null until it is captured again.
+NCU_TRAFFIC = {
+    "rk3_sweep2d": (127.72e6, "paper_2106_07694_gb300/csrc/transport_sweep2d.cuh", "83e0464e30c5"),
+    "lbm_collide_stream": (646.51e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "b6edf2bfe444"),
+}
+
+
+def kernel_traffic(name):
+    import hashlib
+    if name not in NCU_TRAFFIC:
+        return None
+    nbytes, src, sha = NCU_TRAFFIC[name]
+    try:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            cur = hashlib.sha1(fh.read()).hexdigest()[:12]
+    except OSError:
+        return None
+    return nbytes if cur == sha else None
+
+
 def run_oracle_sample(wl, steps, threads):
     """Time the FP64 CPU oracle on the full lattice for `steps` steps (after 1 warm-up)."""
     os.environ["OMP_NUM_THREADS"] = str(threads)
@@ -209,21 +231,39 @@ def bench_ours(args):
         kernels[k]["share"] = t / tot if tot > 0 else None
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     peak, peak_kind = load_peaks()
-    # Algorithmic bytes per node of each kernel family (FP32): populations in+out and c in
-    # for the fluid kernel; c in + c out for the fused transport; per-stage kernels read the
-    # stage input and write the stage output.
-    alg_bytes = {"lbm_collide_stream": 2 * 9 * 4 + 4, "rk3_sweep2d": 8, "rk_stage1": 8, "rk_stage2": 12,
-                 "rk_stage3": 12}
-    roofline = None
-    if dominant in alg_bytes:
-        avg_s = stats[dominant][1] * 1e-3 / stats[dominant][0]
-        achieved = alg_bytes[dominant] * wl.nodes / avg_s / 1e9
-        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
-                    "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                    "alg_bytes_per_node": alg_bytes[dominant]}
     step_ms = t_max / args.steps
-    step_roofline = {"alg_bytes_per_node": 80, "achieved_GBs": 80 * wl.nodes / (step_ms * 1e-3) / 1e9,
-                     "frac_of_measured_hbm": 80 * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
+    # Algorithmic work per node (FP32; derivations in the design doc):
+    #   fluid kernel   76 B (9 populations in and out, c in) and ~260 flop
+    #   RK3 transport  915 flop (3 stages x 2 faces x 2 WENO5-JS reconstructions of 70 flop
+    #                  + split fluxes, diffusion, divergence, Shu-Osher combination); 16 B
+    # FP32 peak: 152 SMs x 128 lanes x 2 flop (FMA) x the SM clock.
+    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
+    ncu_traffic = {k: kernel_traffic(k) for k in ("rk3_sweep2d", "lbm_collide_stream")}
+    def avg_s(name):
+        n_, t_ = stats[name]
+        return t_ * 1e-3 / n_
+    roofline = None
+    if dominant == "rk3_sweep2d":
+        achieved = 915.0 * wl.nodes / avg_s(dominant) / 1e12
+        roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak,
+                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sampled SM clock",
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": ncu_traffic[dominant],
+                    "alg_flop_per_node": 915}
+    elif dominant in ("lbm_collide_stream",):
+        achieved = 76.0 * wl.nodes / avg_s(dominant) / 1e9
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                    "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic.get(dominant), "alg_bytes_per_node": 76}
+    lbm_roofline = None
+    if "lbm_collide_stream" in stats:
+        a_ = 76.0 * wl.nodes / avg_s("lbm_collide_stream") / 1e9
+        lbm_roofline = {"bound": "hbm", "kernel": "lbm_collide_stream", "achieved": a_, "peak": peak,
+                        "unit": "GB/s", "frac": a_ / peak, "traffic": ncu_traffic.get("lbm_collide_stream"),
+                        "alg_bytes_per_node": 76}
+    step_roofline = {"bound": "hbm", "alg_bytes_per_node": 80,
+                     "achieved": 80 * wl.nodes / (step_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": 80 * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
 
     # ---- end to end through the C ABI with host buffers: H2D of c0 (pinned), init,
     # K steps, deposit read and D2H of the final c field, all inside the timed region
@@ -269,7 +309,8 @@ def bench_ours(args):
                        "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
                        "kappa": wl.diffusivity, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (populations 302 MB)"},
-            "roofline": roofline, "step_roofline": step_roofline, "kernels": kernels,
+            "roofline": roofline, "lbm_roofline": lbm_roofline, "step_roofline": step_roofline,
+            "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line), flush=True)
