@@ -212,12 +212,8 @@ def bench_ours(args):
     st = sim.status()
     if st != lw.LW_OK:
         raise RuntimeError(f"device status {st} after the timed region")
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * wl.nodes * args.steps / (t_max * 1e-3) / 1e9
+    from paper_2106_07694_gb300.replicas import job_time_ms, replica_glups
+    value, t_max = replica_glups(ms, wl.nodes, args.steps, device=dev)
 
     # ---- per-kernel durations: the same K steps again, CUDA events around each launch
     lw.lbm_wenoc_profile_enable(sim.handle, True)
@@ -281,10 +277,7 @@ def bench_ours(args):
     lw.lbm_wenoc_fields(sim2.handle, None, None, c_out)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = job_time_ms(e2e_s * 1e3, device=dev) * 1e-3
     e2e = {"value": world * wl.nodes * args.steps / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": c_host.numel() * 4 / args.steps,
            "d2h_bytes_per_step": (c_out.numel() * 4 + 8) / args.steps,
