@@ -26,8 +26,11 @@ sys.path.insert(0, ROOT)
 
 from paper_2106_07694_gb300 import workloads  # noqa: E402
 
-WL = workloads.MAIN_2D
-METRIC = "coupled LBM+WENO5 GLUPS (2D D2Q9 2048x4096 FP32)"
+WORKLOADS = {
+    "2d": (workloads.MAIN_2D, "coupled LBM+WENO5 GLUPS (2D D2Q9 2048x4096 FP32)", "D2Q9"),
+    "3d": (workloads.MAIN_3D, "coupled LBM+WENO5 GLUPS (3D D3Q19 256x256x512 FP32)", "D3Q19"),
+}
+WL, METRIC, LATTICE = WORKLOADS["2d"]
 UNIT = "GLUPS"
 
 
@@ -120,9 +123,12 @@ def kernel_traffic(name):
 
 
 def run_oracle_sample(wl, steps, threads):
-    """Time the FP64 CPU oracle on the full lattice for `steps` steps (after 1 warm-up)."""
+    """Time the FP64 CPU oracle for `steps` steps (after 1 warm-up): the full 2D lattice,
+    or a 64-node-high slab of the 3D one (the full 3D oracle state would need 12 GB)."""
     os.environ["OMP_NUM_THREADS"] = str(threads)
     import oracle
+    if len(wl.shape) == 3:
+        wl = wl.with_(shape=(wl.shape[0], wl.shape[1], 64))
     s = oracle.OracleSim(wl.shape, **phys_kwargs(wl))
     s.init(wl.initial_c())
     s.step(1)
@@ -142,7 +148,8 @@ def bench_reference(args):
     threads = os.cpu_count() or 1
     os.environ["OMP_NUM_THREADS"] = str(threads)
     import oracle
-    band = WL.with_(shape=(WL.shape[0], 128))
+    # a band of the full horizontal extent, 128 nodes high (2D) / 32 high (3D)
+    band = WL.with_(shape=tuple(WL.shape[:-1]) + ((128 if len(WL.shape) == 2 else 32),))
     s = oracle.OracleSim(band.shape, **phys_kwargs(band))
     s.init(band.initial_c())
     s.step(args.warmup)
@@ -154,11 +161,10 @@ def bench_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WL.name, "nx": WL.shape[0], "ny": WL.shape[1],
-                                        "lattice": "D2Q9", "host_threads": threads,
-                                        "sample_rows": band.shape[1]},
+        "data": "synthetic", "config": {"workload": WL.name, "shape": list(WL.shape), "lattice": LATTICE,
+                                        "host_threads": threads, "sample_shape": list(band.shape)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"FP64 C oracle, {band.shape[0]}x{band.shape[1]} band of the "
+                         "sample": f"FP64 C oracle, {'x'.join(map(str, band.shape))} band of the "
                                    f"workload, {args.steps} steps after {args.warmup} warm-up"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -229,37 +235,46 @@ def bench_ours(args):
     peak, peak_kind = load_peaks()
     step_ms = t_max / args.steps
     # Algorithmic work per node (FP32; derivations in the design doc):
-    #   fluid kernel   76 B (9 populations in and out, c in) and ~260 flop
-    #   RK3 transport  915 flop (3 stages x 2 faces x 2 WENO5-JS reconstructions of 70 flop
-    #                  + split fluxes, diffusion, divergence, Shu-Osher combination); 16 B
-    # FP32 peak: 152 SMs x 128 lanes x 2 flop (FMA) x the SM clock.
+    #   fluid kernel   2 Q 4 B populations in and out + 4 B c in (D2Q9 76 B, D3Q19 156 B)
+    #   RK3 transport  3 stages x dim faces x (2 WENO5-JS reconstructions of 70 flop + split
+    #                  fluxes, diffusion, sum) + divergence and Shu-Osher combination:
+    #                  915 flop in 2D, 1371 flop in 3D (a third per stage kernel)
+    #   whole step     populations in and out + c in and out: 80 B (2D), 160 B (3D)
+    # FP32 peak: 152 SMs x 128 lanes x 2 flop (FMA) x the sampled SM clock.
+    dim = len(wl.shape)
+    lbm_B = 2 * (9 if dim == 2 else 19) * 4 + 4
+    step_B = lbm_B + 4
+    tr_flop = 915.0 if dim == 2 else 1371.0
+    flop_of = {"rk3_sweep2d": tr_flop, "rk3_sweep3d": tr_flop, "rk_stage1": tr_flop / 3,
+               "rk_stage2": tr_flop / 3, "rk_stage3": tr_flop / 3}
     sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
-    ncu_traffic = {k: kernel_traffic(k) for k in ("rk3_sweep2d", "lbm_collide_stream")}
+    ncu_traffic = {k: kernel_traffic(k) if dim == 2 else None for k in ("rk3_sweep2d", "lbm_collide_stream")}
+
     def avg_s(name):
         n_, t_ = stats[name]
         return t_ * 1e-3 / n_
     roofline = None
-    if dominant == "rk3_sweep2d":
-        achieved = 915.0 * wl.nodes / avg_s(dominant) / 1e12
+    if dominant in flop_of:
+        achieved = flop_of[dominant] * wl.nodes / avg_s(dominant) / 1e12
         roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak,
                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sampled SM clock",
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": ncu_traffic[dominant],
-                    "alg_flop_per_node": 915}
-    elif dominant in ("lbm_collide_stream",):
-        achieved = 76.0 * wl.nodes / avg_s(dominant) / 1e9
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": ncu_traffic.get(dominant),
+                    "alg_flop_per_node": flop_of[dominant]}
+    elif dominant == "lbm_collide_stream":
+        achieved = lbm_B * wl.nodes / avg_s(dominant) / 1e9
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                     "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": ncu_traffic.get(dominant), "alg_bytes_per_node": 76}
+                    "traffic": ncu_traffic.get(dominant), "alg_bytes_per_node": lbm_B}
     lbm_roofline = None
     if "lbm_collide_stream" in stats:
-        a_ = 76.0 * wl.nodes / avg_s("lbm_collide_stream") / 1e9
+        a_ = lbm_B * wl.nodes / avg_s("lbm_collide_stream") / 1e9
         lbm_roofline = {"bound": "hbm", "kernel": "lbm_collide_stream", "achieved": a_, "peak": peak,
                         "unit": "GB/s", "frac": a_ / peak, "traffic": ncu_traffic.get("lbm_collide_stream"),
-                        "alg_bytes_per_node": 76}
-    step_roofline = {"bound": "hbm", "alg_bytes_per_node": 80,
-                     "achieved": 80 * wl.nodes / (step_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": 80 * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
+                        "alg_bytes_per_node": lbm_B}
+    step_roofline = {"bound": "hbm", "alg_bytes_per_node": step_B,
+                     "achieved": step_B * wl.nodes / (step_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": step_B * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
 
     # ---- end to end through the C ABI with host buffers: H2D of c0 (pinned), init,
     # K steps, deposit read and D2H of the final c field, all inside the timed region
@@ -290,7 +305,8 @@ def bench_ours(args):
         threads = os.cpu_count() or 1
         v, dt = run_oracle_sample(wl, args.cpu_steps, threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"FP64 C oracle on the full {wl.shape[0]}x{wl.shape[1]} lattice, "
+               "sample": f"FP64 C oracle, {'x'.join(map(str, wl.shape[:-1]))}x"
+                         f"{wl.shape[-1] if len(wl.shape) == 2 else 64} lattice, "
                          f"{args.cpu_steps} steps after 1 warm-up ({dt:.1f} s)"}
 
     if rank == 0:
@@ -298,10 +314,10 @@ def bench_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "nx": wl.shape[0], "ny": wl.shape[1], "lattice": "D2Q9",
+            "config": {"workload": wl.name, "shape": list(wl.shape), "lattice": LATTICE,
                        "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
                        "kappa": wl.diffusivity, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (populations 302 MB)"},
+                       "l2": f"inputs larger than L2 (populations {wl.nodes * (9 if len(wl.shape) == 2 else 19) * 4 / 1e6:.0f} MB)"},
             "roofline": roofline, "lbm_roofline": lbm_roofline, "step_roofline": step_roofline,
             "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
@@ -320,7 +336,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS),
+                    help="2d: the 2048x4096 D2Q9 case the metric is quoted on; 3d: 256x256x512 D3Q19")
     args = ap.parse_args()
+    global WL, METRIC, LATTICE
+    WL, METRIC, LATTICE = WORKLOADS[args.workload]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

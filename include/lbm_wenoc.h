@@ -38,7 +38,7 @@ extern "C" {
 #endif
 
 #define LW_OK 0
-#define LW_EINVAL -1    /* bad argument or parameter (e.g. tau <= 1/2, nx % 4 != 0) */
+#define LW_EINVAL -1    /* bad argument or parameter (e.g. tau <= 1/2, nx % 4 != 0, Q*nodes >= 2^31) */
 #define LW_ENOMEM -2    /* workspace smaller than lbm_wenoc_workspace_bytes() */
 #define LW_ECUDA -3     /* a CUDA runtime call failed */
 #define LW_EUNSTABLE -4 /* device status: non-finite value or |u_d| > u_cap */
@@ -128,9 +128,10 @@ int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, in
 /* Number of kernel launches this handle has issued since create. */
 int64_t lbm_wenoc_launch_count(const lbm_wenoc* h);
 
-/* Tuning of the fused 2D FP32 transport kernel: rows per CTA segment (0 = default,
- * about two CTAs per SM in one wave).  Results do not depend on it (bitwise).  No
- * effect on other paths.  Drops captured graphs; call between steps. */
+/* Tuning of the FP32 transport sweeps: rows per CTA segment of the fused 2D kernel, or
+ * z levels per CTA segment of the 3D stage kernels (0 = default).  Results do not
+ * depend on it (bitwise).  No effect on FP64 or periodic-vertical handles.  Drops
+ * captured graphs; call between steps. */
 int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows);
 
 /* Sum of a concentration field, FP64, for callers that cannot allocate device memory

@@ -215,6 +215,83 @@ __global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
   }
 }
 
+// D3Q19 specialisation (same arithmetic as lbm_step_kernel): 32-bit offsets with the
+// neighbour offsets along x, y (periodic) and z (walls or periodic) hoisted, the wall
+// tests taken once per block (a block is one x segment of one (y, z) row), streaming
+// cache hints on the population traffic.
+template <typename T, int PARITY>
+__global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  if (x >= nx) return;
+  const unsigned n = (unsigned)a.n;
+  const int plane = nx * ny;
+  const unsigned node = (unsigned)z * (unsigned)plane + (unsigned)y * (unsigned)nx + (unsigned)x;
+  const bool walls = a.walls != 0;
+  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? -(nx - 1) : 1;
+  const int dym = y == 0 ? (ny - 1) * nx : -nx, dyp = y == ny - 1 ? -(ny - 1) * nx : nx;
+  const bool bot = z == 0, top = z == nz - 1;
+  const int dzm = bot ? (walls ? 0 : (nz - 1) * plane) : -plane;
+  const int dzp = top ? (walls ? 0 : -(nz - 1) * plane) : plane;
+  const bool wall_m = walls && bot, wall_p = walls && top;
+  T* __restrict__ G = a.g;
+  auto off = [&](int i, int s) -> int {
+    const int cx = s * D3Q19::cx(i), cy = s * D3Q19::cy(i), cz = s * D3Q19::cz(i);
+    return (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) +
+           (cz > 0 ? dzp : (cz < 0 ? dzm : 0));
+  };
+  auto behind_wall = [&](int i, int s) -> bool {
+    const int cz = s * D3Q19::cz(i);
+    return (cz < 0 && wall_m) || (cz > 0 && wall_p);
+  };
+  T g[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    if (PARITY == 0) {
+      g[i] = __ldcs(G + i * n + node);
+    } else {
+      g[i] = behind_wall(i, -1) ? __ldcs(G + i * n + node)
+                                : __ldcs(G + D3Q19::opp(i) * n + (unsigned)((int)node + off(i, -1)));
+    }
+  }
+  T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    drho += g[i];
+    if (D3Q19::cx(i)) jx += D3Q19::cx(i) * g[i];
+    if (D3Q19::cy(i)) jy += D3Q19::cy(i) * g[i];
+    if (D3Q19::cz(i)) jz += D3Q19::cz(i) * g[i];
+  }
+  const T Fx = a.bf[0], Fy = a.bf[1], Fz = a.bf[2] - a.A * a.c[node];
+  const T rho = T(1) + drho;
+  const T inv_rho = T(1) / rho;
+  const T ux = (jx + T(0.5) * Fx) * inv_rho, uy = (jy + T(0.5) * Fy) * inv_rho, uz = (jz + T(0.5) * Fz) * inv_rho;
+  a.u[node] = ux;
+  a.u[n + node] = uy;
+  a.u[2 * n + node] = uz;
+  report_status(a.status, !finite_val(rho) || !(fabs(ux) <= a.u_cap) || !(fabs(uy) <= a.u_cap) ||
+                              !(fabs(uz) <= a.u_cap));
+  const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const T wi = T(D3Q19::w(i));
+    const T cu = D3Q19::cx(i) * ux + D3Q19::cy(i) * uy + D3Q19::cz(i) * uz;
+    const T cF = D3Q19::cx(i) * Fx + D3Q19::cy(i) * Fy + D3Q19::cz(i) * Fz;
+    const T geq = wi * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    const T src = a.guo * wi * (T(3) * (cF - uF) + T(9) * cu * cF);
+    const T gs = g[i] - a.omega * (g[i] - geq) + src;
+    if (PARITY == 0) {
+      __stcs(G + D3Q19::opp(i) * n + node, gs);
+    } else {
+      if (behind_wall(i, +1))
+        __stcs(G + D3Q19::opp(i) * n + node, gs);
+      else
+        __stcs(G + i * n + (unsigned)((int)node + off(i, +1)), gs);
+    }
+  }
+}
+
 // Macroscopic fields of the current state (parity as in load_populations):
 // rho, u = (sum g c + F/2)/rho with the current c.
 template <class LAT, typename T, int PARITY>

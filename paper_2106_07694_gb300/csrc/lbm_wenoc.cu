@@ -19,6 +19,7 @@
 #include "reduce_kernels.cuh"
 #include "transport_kernels.cuh"
 #include "transport_sweep2d.cuh"
+#include "transport_sweep3d.cuh"
 
 namespace {
 
@@ -87,6 +88,7 @@ int check_params(const lbm_wenoc_params* p) {
   if (!(p->lf_alpha >= 0.0) || !(p->u_cap >= 0.0)) return LW_EINVAL;
   const double nn = (double)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   if (nn > 4.0e9) return LW_EINVAL;
+  if ((double)(p->dim == 2 ? 9 : 19) * nn >= 2147483647.0) return LW_EINVAL;  // 32-bit population offsets
   return LW_OK;
 }
 
@@ -104,6 +106,8 @@ struct lbm_wenoc {
   int cur = 0;     // which buffer holds c^n: 0 = c, 1 = c1 (2D FP32 sweep path ping-pongs)
   bool sweep = false;
   lw::SweepLaunch sweep_geom{};
+  bool sweep3d = false;  // 3D FP32 with walls: tiled z-sweep stage kernels
+  int sweep3d_rows = 0;
   bool initialised = false;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -162,6 +166,7 @@ Args<T> make_args(const lbm_wenoc* h) {
 enum Kind { K_LBM = 0, K_STAGE1, K_STAGE2, K_STAGE3, K_DEPOSIT, K_RK3_SWEEP, K_OTHER, K_COUNT };
 const char* kKindNames[K_COUNT] = {"lbm_collide_stream", "rk_stage1", "rk_stage2", "rk_stage3",
                                    "deposit_reduce", "rk3_sweep2d", "other"};
+// The 3D FP32 stage kernels are timed under the rk_stage* names.
 
 cudaEvent_t take_event(lbm_wenoc* h) {
   if (h->event_pool.empty()) {
@@ -223,9 +228,9 @@ void enqueue_step(lbm_wenoc* h, int parity) {
           lw::lbm_d2q9_kernel<T, 1><<<grd, blk, 0, s>>>(a);
       } else {
         if (parity == 0)
-          lw::lbm_step_kernel<LAT, T, 0><<<grd, blk, 0, s>>>(a);
+          lw::lbm_d3q19_kernel<T, 0><<<grd, blk, 0, s>>>(a);
         else
-          lw::lbm_step_kernel<LAT, T, 1><<<grd, blk, 0, s>>>(a);
+          lw::lbm_d3q19_kernel<T, 1><<<grd, blk, 0, s>>>(a);
       }
     });
   }
@@ -236,6 +241,17 @@ void enqueue_step(lbm_wenoc* h, int parity) {
     float* c_out = reinterpret_cast<float*>(h->ws + (h->cur ? h->L.c : h->L.c1));
     launch(h, K_RK3_SWEEP, [&] { lw::launch_sweep2d(af, c_out, h->sweep_geom, s); });
     h->cur ^= 1;
+    return;
+  }
+  if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d) {
+    const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
+    const int H = h->sweep3d_rows;
+    launch(h, K_STAGE1, [&] { lw::launch_sweep3d<1>(af, af.c, af.c1, H, s); });
+    launch(h, K_STAGE2, [&] { lw::launch_sweep3d<2>(af, af.c1, af.c2, H, s); });
+    launch(h, K_DEPOSIT, [&] {
+      lw::deposit_kernel<T><<<dep_blocks, lw::kReduceThreads, 0, s>>>(a, nfloor);
+    });
+    launch(h, K_STAGE3, [&] { lw::launch_sweep3d<3>(af, af.c2, af.c, H, s); });
     return;
   }
   launch(h, K_STAGE1, [&] { lw::rk_stage_kernel<T, LAT::DIM, 1><<<grd, blk, 0, s>>>(a); });
@@ -383,6 +399,16 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
     h->sweep_geom = lw::sweep2d_geometry(p->nx, p->ny, sms, 0);
     if (cudaFuncSetAttribute(lw::rk3_sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lw::sweep2d_smem()) != cudaSuccess) {
+      delete h;
+      return LW_ECUDA;
+    }
+  }
+  h->sweep3d = !h->fp64 && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
+  if (h->sweep3d) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
+    h->sweep3d_rows = lw::sweep3d_rows(p->nx, p->ny, p->nz, sms, 0);
+    if (lw::sweep3d_prepare() != cudaSuccess) {
       delete h;
       return LW_ECUDA;
     }
@@ -586,6 +612,14 @@ int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, in
 
 int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows) {
   if (!h || rows < 0) return LW_EINVAL;
+  if (h->sweep3d) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+    destroy_graphs(h);
+    h->sweep3d_rows = lw::sweep3d_rows(h->p.nx, h->p.ny, h->p.nz, sms, rows);
+    return LW_OK;
+  }
   if (!h->sweep) return LW_OK;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;

@@ -1,0 +1,253 @@
+// 3D FP32 transport: one SSP-RK3 stage of the WENO5 + diffusion + settling update of c
+// (steps a4..a8) as a tiled sweep along the vertical axis z.
+//
+// A CTA owns a 32 x 8 tile of (x, y) columns and a segment of z levels and sweeps it
+// upward.  At level k it stages the x- and y-split fluxes of the stage input on the
+// tile plus a 3-column halo in shared memory (loaded from L2), computes the left
+// x face and the lower y face of every column (the tile's right and upper edge faces by
+// two dedicated warps), and the upper z face of its own column from a per-column ring
+// of z-split fluxes that runs three levels ahead; the lower z face is carried from the
+// previous level.  Every face of the stage is computed once.  Three launches make a
+// step (the intermediate fields go through HBM/L2); the stage kernels of the generic
+// path (transport_kernels.cuh) remain for FP64, periodic-vertical and 2D.
+//
+// Walls as in the rest of the library: ghost levels -2, -1, nz, nz+1 reflect c (even)
+// and the fluid velocity (odd, Vs unchanged); the floor face carries -Vs c(0), the lid 0.
+#pragma once
+#include "common.cuh"
+#include "transport_sweep2d.cuh"  // weno5_face_value, face_flux_x
+
+namespace lw {
+
+constexpr int kT3x = 32, kT3y = 8;           // tile (threads)
+constexpr int kT3h = 3;                      // stencil radius
+constexpr int kT3X = kT3x + 2 * kT3h;        // tile + halo, x
+constexpr int kT3Y = kT3y + 2 * kT3h;        // tile + halo, y
+constexpr int kT3r = 8;                      // z ring depth
+
+struct Sweep3dSmem {
+  float xp[kT3y][kT3X];  // x-split h+/alpha, tile rows, x halo
+  float xm[kT3y][kT3X];
+  float yp[kT3Y][kT3x];  // y-split, tile columns, y halo
+  float ym[kT3Y][kT3x];
+  float c[kT3Y][kT3X];   // stage input value (diffusion)
+  float zp[kT3r][kT3y][kT3x];  // z-split ring of each column
+  float zm[kT3r][kT3y][kT3x];
+  float cz[kT3r][kT3y][kT3x];  // stage input value ring of each column
+  float fx[kT3y][kT3x + 1];    // left x faces (+ right edge)
+  float fy[kT3y + 1][kT3x];    // lower y faces (+ upper edge)
+};
+
+struct Sweep3dParams {
+  const float* cin;  // stage input field (c, c1 or c2)
+  float* cout;       // stage output field (c1, c2 or c in place)
+  int H;             // z levels per segment
+  float ghost_shift; // 2 Vs / alpha
+};
+
+template <int STAGE>
+__global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, Sweep3dParams sp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sweep3dSmem& S = *reinterpret_cast<Sweep3dSmem*>(smem_raw);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kT3x + tx;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int x0 = blockIdx.x * kT3x, y0 = blockIdx.y * kT3y;
+  const int z0 = blockIdx.z * sp.H, z1 = min(nz, z0 + sp.H);
+  const int X = (x0 + tx) % nx, Y = (y0 + ty) % ny;
+  const bool out = (x0 + tx) < nx && (y0 + ty) < ny;
+  const unsigned plane = (unsigned)nx * (unsigned)ny, n = (unsigned)a.n;
+  const float inv_alpha = a.inv_alpha, vs_a = a.vs * a.inv_alpha, alpha = a.alpha, kappa = a.kappa;
+  const float* __restrict__ cin = sp.cin;
+  const float* __restrict__ ux = a.u;
+  const float* __restrict__ uy = a.u + n;
+  const float* __restrict__ uz = a.u + 2 * n;
+  const unsigned col = (unsigned)Y * (unsigned)nx + (unsigned)X;
+
+  // own column, level l (ghosts reflect): c and scaled vertical transport velocity,
+  // loaded one level before they enter the ring (software pipelining)
+  float qc = 0.f, qw = 0.f, qn = 0.f;
+  auto col_fetch = [&](int l) {
+    const bool ghost = l < 0 || l >= nz;
+    const int lr = l < 0 ? -1 - l : (l >= nz ? 2 * nz - 1 - l : l);
+    const unsigned k = (unsigned)lr * plane + col;
+    qc = __ldg(cin + k);
+    const float u = __ldg(uz + k);
+    qw = fmaf(ghost ? -u : u, inv_alpha, -vs_a);
+  };
+  auto col_put = [&](int l) {
+    const float h = 0.5f * qc;
+    S.zp[l & (kT3r - 1)][ty][tx] = fmaf(qw, h, h);
+    S.zm[l & (kT3r - 1)][ty][tx] = fmaf(qw, h, -h);
+    S.cz[l & (kT3r - 1)][ty][tx] = qc;
+  };
+  auto col_split = [&](int l) {
+    col_fetch(l);
+    col_put(l);
+  };
+  // c^n at the own column, one level ahead (stages 2 and 3 combine with it)
+  auto cn_fetch = [&](int k) {
+    if (STAGE > 1 && k < z1) qn = a.c[(unsigned)k * plane + col];
+  };
+
+  // Each thread stages up to three positions of the tile + halo cross (the corners are
+  // not needed); their smem slots and in-plane offsets are fixed for the whole sweep.
+  constexpr int kSlots = (kT3X * kT3Y + kT3x * kT3y - 1) / (kT3x * kT3y);
+  int sl_ry[kSlots], sl_rx[kSlots];
+  unsigned sl_off[kSlots];
+  bool sl_x[kSlots], sl_y[kSlots], sl_on[kSlots];
+#pragma unroll
+  for (int q = 0; q < kSlots; ++q) {
+    const int j = tid + q * kT3x * kT3y;
+    const int rx = j % kT3X, ry = j / kT3X;
+    sl_rx[q] = rx;
+    sl_ry[q] = ry;
+    sl_x[q] = ry >= kT3h && ry < kT3h + kT3y;
+    sl_y[q] = rx >= kT3h && rx < kT3h + kT3x;
+    sl_on[q] = j < kT3X * kT3Y && (sl_x[q] || sl_y[q]);
+    const int gx = (x0 - kT3h + rx + 4 * nx) % nx, gy = (y0 - kT3h + ry + 4 * ny) % ny;
+    sl_off[q] = (unsigned)gy * (unsigned)nx + (unsigned)gx;
+  }
+  // registers holding the next level's staged values (software pipelining)
+  float pc[kSlots], pu[kSlots], pv[kSlots];
+  auto fetch_tile = [&](int k) {
+    const unsigned lv = (unsigned)k * plane;
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) {
+      if (sl_on[q] && k < z1) {
+        const unsigned k3 = lv + sl_off[q];
+        pc[q] = __ldg(cin + k3);
+        pu[q] = sl_x[q] ? __ldg(ux + k3) : 0.f;
+        pv[q] = sl_y[q] ? __ldg(uy + k3) : 0.f;
+      }
+    }
+  };
+
+  const int kb = z0 == 0 ? 0 : z0 - 1;  // first level: z0, or the priming level below it
+  for (int l = kb - 2; l < kb + 3; ++l) col_split(l);
+  col_fetch(kb + 3);
+  float carry = 0.f;
+  fetch_tile(kb);
+  cn_fetch(kb);
+
+  for (int k = kb; k < z1; ++k) {
+    const bool prime = k < z0;
+    const unsigned lv = (unsigned)k * plane;
+    // ---- stage the tile and its halo at level k (prefetched); own column three levels ahead
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) {
+      if (sl_on[q]) {
+        const float c = pc[q], h = 0.5f * c;
+        const int rx = sl_rx[q], ry = sl_ry[q];
+        S.c[ry][rx] = c;
+        if (sl_x[q]) {
+          const float w = pu[q] * inv_alpha;
+          S.xp[ry - kT3h][rx] = fmaf(w, h, h);
+          S.xm[ry - kT3h][rx] = fmaf(w, h, -h);
+        }
+        if (sl_y[q]) {
+          const float w = pv[q] * inv_alpha;
+          S.yp[ry][rx - kT3h] = fmaf(w, h, h);
+          S.ym[ry][rx - kT3h] = fmaf(w, h, -h);
+        }
+      }
+    }
+    fetch_tile(k + 1);
+    col_put(k + 3);
+    col_fetch(k + 4);
+    const float cn_here = qn;
+    cn_fetch(k + 1);
+    __syncthreads();
+
+    // ---- faces: left x face and lower y face of this column, upper z face
+    if (!prime) {
+      const float* P = &S.xp[ty][tx];
+      const float* M = &S.xm[ty][tx];
+      S.fx[ty][tx] = face_flux_x(P[0], P[1], P[2], P[3], P[4], M[5], M[4], M[3], M[2], M[1], alpha, kappa,
+                                 S.c[ty + kT3h][tx + kT3h - 1], S.c[ty + kT3h][tx + kT3h]);
+      S.fy[ty][tx] = face_flux_x(S.yp[ty][tx], S.yp[ty + 1][tx], S.yp[ty + 2][tx], S.yp[ty + 3][tx],
+                                 S.yp[ty + 4][tx], S.ym[ty + 5][tx], S.ym[ty + 4][tx], S.ym[ty + 3][tx],
+                                 S.ym[ty + 2][tx], S.ym[ty + 1][tx], alpha, kappa, S.c[ty + kT3h - 1][tx + kT3h],
+                                 S.c[ty + kT3h][tx + kT3h]);
+      if (ty == 0 && tx < kT3y) {  // right edge x faces (column 32) of the tile rows
+        const float* Pe = &S.xp[tx][kT3x];
+        const float* Me = &S.xm[tx][kT3x];
+        S.fx[tx][kT3x] = face_flux_x(Pe[0], Pe[1], Pe[2], Pe[3], Pe[4], Me[5], Me[4], Me[3], Me[2], Me[1], alpha,
+                                     kappa, S.c[tx + kT3h][kT3x + kT3h - 1], S.c[tx + kT3h][kT3x + kT3h]);
+      }
+      if (ty == 1) {  // upper edge y faces (row 8) of the tile columns
+        S.fy[kT3y][tx] = face_flux_x(S.yp[kT3y][tx], S.yp[kT3y + 1][tx], S.yp[kT3y + 2][tx], S.yp[kT3y + 3][tx],
+                                     S.yp[kT3y + 4][tx], S.ym[kT3y + 5][tx], S.ym[kT3y + 4][tx],
+                                     S.ym[kT3y + 3][tx], S.ym[kT3y + 2][tx], S.ym[kT3y + 1][tx], alpha, kappa,
+                                     S.c[kT3y + kT3h - 1][tx + kT3h], S.c[kT3y + kT3h][tx + kT3h]);
+      }
+    }
+    const float chere = S.cz[k & (kT3r - 1)][ty][tx];
+    float fup = 0.f;
+    if (k != nz - 1) {
+      fup = face_flux_x(S.zp[(k - 2) & (kT3r - 1)][ty][tx], S.zp[(k - 1) & (kT3r - 1)][ty][tx],
+                        S.zp[k & (kT3r - 1)][ty][tx], S.zp[(k + 1) & (kT3r - 1)][ty][tx],
+                        S.zp[(k + 2) & (kT3r - 1)][ty][tx], S.zm[(k + 3) & (kT3r - 1)][ty][tx],
+                        S.zm[(k + 2) & (kT3r - 1)][ty][tx], S.zm[(k + 1) & (kT3r - 1)][ty][tx],
+                        S.zm[k & (kT3r - 1)][ty][tx], S.zm[(k - 1) & (kT3r - 1)][ty][tx], alpha, kappa, chere,
+                        S.cz[(k + 1) & (kT3r - 1)][ty][tx]);
+    }
+    __syncthreads();
+
+    // ---- divergence and the Shu-Osher combination of this stage
+    if (!prime) {
+      const float fdn = k == 0 ? -a.vs * chere : carry;
+      const float L = S.fx[ty][tx] - S.fx[ty][tx + 1] + S.fy[ty][tx] - S.fy[ty + 1][tx] + fdn - fup;
+      if (out) {
+        const unsigned node = lv + col;
+        float v;
+        if (STAGE == 1) {
+          v = chere + L;
+        } else if (STAGE == 2) {
+          v = fmaf(0.75f, cn_here, 0.25f * (chere + L));
+        } else {
+          const float s = chere + L;
+          v = fmaf(1.f / 3.f, cn_here - s, s);
+        }
+        sp.cout[node] = v;
+        if (STAGE == 3) report_status(a.status, !isfinite(v));
+      }
+    }
+    carry = fup;
+  }
+}
+
+inline size_t sweep3d_smem() { return sizeof(Sweep3dSmem); }
+
+inline bool sweep3d_supported(int nz, bool walls) { return walls && nz >= 4; }
+
+inline cudaError_t sweep3d_prepare() {
+  const int b = (int)sizeof(Sweep3dSmem);
+  cudaError_t e = cudaFuncSetAttribute(rk_sweep3d_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
+}
+
+inline int sweep3d_rows(int nx, int ny, int nz, int sm_count, int override_rows) {
+  if (override_rows > 0) return min(override_rows, nz);
+  const long long tiles = (long long)((nx + kT3x - 1) / kT3x) * ((ny + kT3y - 1) / kT3y);
+  // at least sixteen CTAs per SM in total (four waves at four resident CTAs per SM),
+  // segments no shorter than 24 levels
+  long long segs = (16LL * sm_count + tiles - 1) / tiles;
+  int H = (int)((nz + segs - 1) / segs);
+  return max(min(24, nz), H);
+}
+
+template <int STAGE>
+inline cudaError_t launch_sweep3d(const Args<float>& a, const float* cin, float* cout, int H, cudaStream_t s) {
+  Sweep3dParams sp;
+  sp.cin = cin;
+  sp.cout = cout;
+  sp.H = H;
+  sp.ghost_shift = 2.f * a.vs * a.inv_alpha;
+  const dim3 grid((a.nx + kT3x - 1) / kT3x, (a.ny + kT3y - 1) / kT3y, (a.nz + H - 1) / H);
+  rk_sweep3d_kernel<STAGE><<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
+  return cudaGetLastError();
+}
+
+}  // namespace lw
