@@ -272,6 +272,15 @@ def bench_ours(args):
         lbm_roofline = {"bound": "hbm", "kernel": "lbm_collide_stream", "achieved": a_, "peak": peak,
                         "unit": "GB/s", "frac": a_ / peak, "traffic": ncu_traffic.get("lbm_collide_stream"),
                         "alg_bytes_per_node": lbm_B}
+    # the transport as a whole (one fused kernel or three stage kernels) against the FP32 peak
+    tr_kernels = [k for k in ("rk3_sweep2d", "rk_stage1", "rk_stage2", "rk_stage3") if k in stats]
+    transport_roofline = None
+    if tr_kernels:
+        t_tr = sum(avg_s(k) for k in tr_kernels)
+        a_ = tr_flop * wl.nodes / t_tr / 1e12
+        transport_roofline = {"bound": "alu", "kernels": tr_kernels, "achieved": a_, "peak": fp32_peak,
+                              "unit": "TFLOP/s", "frac": a_ / fp32_peak, "alg_flop_per_node": tr_flop,
+                              "us_per_step": t_tr * 1e6}
     step_roofline = {"bound": "hbm", "alg_bytes_per_node": step_B,
                      "achieved": step_B * wl.nodes / (step_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": step_B * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
@@ -318,7 +327,8 @@ def bench_ours(args):
                        "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
                        "kappa": wl.diffusivity, "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 (populations {wl.nodes * (9 if len(wl.shape) == 2 else 19) * 4 / 1e6:.0f} MB)"},
-            "roofline": roofline, "lbm_roofline": lbm_roofline, "step_roofline": step_roofline,
+            "roofline": roofline, "lbm_roofline": lbm_roofline, "transport_roofline": transport_roofline,
+            "step_roofline": step_roofline,
             "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         }

@@ -49,6 +49,8 @@ extern "C" {
 #define LW_PERIODIC_VERTICAL 0x2u /* vertical axis periodic too: no walls, no deposit (tests) */
 #define LW_FROZEN_VELOCITY 0x4u   /* fluid not advanced; c transported by the u given at init (tests) */
 #define LW_NO_GRAPH 0x8u          /* launch kernels one by one instead of replaying CUDA graphs */
+#define LW_FUSED_RK3 0x10u        /* 2D FP32: the three RK stages in one fused sweep kernel instead of
+                                     three row-sweep launches (same results to rounding) */
 
 typedef struct lbm_wenoc lbm_wenoc; /* opaque host-side handle */
 
@@ -63,7 +65,7 @@ typedef struct {
   double lf_alpha;           /* Lax-Friedrichs split speed; 0 selects settling_velocity + u_cap */
   double u_cap;              /* bound on |u_d| checked on the device; 0 selects 0.1 */
   double body_force[3];      /* extra uniform force (e.g. a channel flow), added to the buoyancy */
-  uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH */
+  uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH | LW_FUSED_RK3 */
 } lbm_wenoc_params;
 
 /* Bytes of device workspace a handle with these parameters needs (populations,

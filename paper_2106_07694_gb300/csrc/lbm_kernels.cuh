@@ -196,14 +196,8 @@ __global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
   a.u[n + node] = uy;
   report_status(a.status, !finite_val(rho) || !(fabs(ux) <= a.u_cap) || !(fabs(uy) <= a.u_cap));
   const T uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const T wi = T(D2Q9::w(i));
-    const T cu = D2Q9::cx(i) * ux + D2Q9::cy(i) * uy;
-    const T cF = D2Q9::cx(i) * Fx + D2Q9::cy(i) * Fy;
-    const T geq = wi * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-    const T src = a.guo * wi * (T(3) * (cF - uF) + T(9) * cu * cF);
-    const T gs = g[i] - a.omega * (g[i] - geq) + src;
+  const T om = a.omega, keep = T(1) - a.omega;
+  auto store = [&](int i, T gs) {
     if (PARITY == 0) {
       __stcs(G + D2Q9::opp(i) * n + node, gs);
     } else {
@@ -212,6 +206,27 @@ __global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
       else
         __stcs(G + i * n + (unsigned)((int)node + off(i, +1)), gs);
     }
+  };
+  // rest population
+  {
+    const T w0 = T(D2Q9::w(0));
+    const T geq = w0 * (drho - rho * T(1.5) * uu);
+    const T src = a.guo * w0 * (T(-3) * uF);
+    store(0, keep * g[0] + om * geq + src);
+  }
+  // opposite pairs (i, i+1) share c.u and c.F up to sign: split the equilibrium and
+  // the Guo source into parts even and odd in c_i
+#pragma unroll
+  for (int i = 1; i < 9; i += 2) {
+    const T wi = T(D2Q9::w(i));
+    const T cu = D2Q9::cx(i) * ux + D2Q9::cy(i) * uy;
+    const T cF = D2Q9::cx(i) * Fx + D2Q9::cy(i) * Fy;
+    const T even = wi * (drho + rho * (T(4.5) * cu * cu - T(1.5) * uu));
+    const T odd = wi * rho * T(3) * cu;
+    const T seven = a.guo * wi * (T(9) * cu * cF - T(3) * uF);
+    const T sodd = a.guo * wi * T(3) * cF;
+    store(i, keep * g[i] + om * (even + odd) + (seven + sodd));
+    store(i + 1, keep * g[i + 1] + om * (even - odd) + (seven - sodd));
   }
 }
 
@@ -273,14 +288,8 @@ __global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
   report_status(a.status, !finite_val(rho) || !(fabs(ux) <= a.u_cap) || !(fabs(uy) <= a.u_cap) ||
                               !(fabs(uz) <= a.u_cap));
   const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
-#pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    const T wi = T(D3Q19::w(i));
-    const T cu = D3Q19::cx(i) * ux + D3Q19::cy(i) * uy + D3Q19::cz(i) * uz;
-    const T cF = D3Q19::cx(i) * Fx + D3Q19::cy(i) * Fy + D3Q19::cz(i) * Fz;
-    const T geq = wi * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-    const T src = a.guo * wi * (T(3) * (cF - uF) + T(9) * cu * cF);
-    const T gs = g[i] - a.omega * (g[i] - geq) + src;
+  const T om = a.omega, keep = T(1) - a.omega;
+  auto store = [&](int i, T gs) {
     if (PARITY == 0) {
       __stcs(G + D3Q19::opp(i) * n + node, gs);
     } else {
@@ -289,6 +298,24 @@ __global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
       else
         __stcs(G + i * n + (unsigned)((int)node + off(i, +1)), gs);
     }
+  };
+  {
+    const T w0 = T(D3Q19::w(0));
+    const T geq = w0 * (drho - rho * T(1.5) * uu);
+    const T src = a.guo * w0 * (T(-3) * uF);
+    store(0, keep * g[0] + om * geq + src);
+  }
+#pragma unroll
+  for (int i = 1; i < 19; i += 2) {  // opposite pairs (i, i+1)
+    const T wi = T(D3Q19::w(i));
+    const T cu = D3Q19::cx(i) * ux + D3Q19::cy(i) * uy + D3Q19::cz(i) * uz;
+    const T cF = D3Q19::cx(i) * Fx + D3Q19::cy(i) * Fy + D3Q19::cz(i) * Fz;
+    const T even = wi * (drho + rho * (T(4.5) * cu * cu - T(1.5) * uu));
+    const T odd = wi * rho * T(3) * cu;
+    const T seven = a.guo * wi * (T(9) * cu * cF - T(3) * uF);
+    const T sodd = a.guo * wi * T(3) * cF;
+    store(i, keep * g[i] + om * (even + odd) + (seven + sodd));
+    store(i + 1, keep * g[i + 1] + om * (even - odd) + (seven - sodd));
   }
 }
 

@@ -20,6 +20,7 @@
 #include "transport_kernels.cuh"
 #include "transport_sweep2d.cuh"
 #include "transport_sweep3d.cuh"
+#include "transport_stage2d.cuh"
 
 namespace {
 
@@ -108,6 +109,8 @@ struct lbm_wenoc {
   lw::SweepLaunch sweep_geom{};
   bool sweep3d = false;  // 3D FP32 with walls: tiled z-sweep stage kernels
   int sweep3d_rows = 0;
+  bool stage2d = false;  // 2D FP32 with walls: three row-sweep stage kernels
+  int stage2d_rows = 0;
   bool initialised = false;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -243,6 +246,14 @@ void enqueue_step(lbm_wenoc* h, int parity) {
     h->cur ^= 1;
     return;
   }
+  if (std::is_same<T, float>::value && LAT::DIM == 2 && h->stage2d) {
+    const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
+    const int H = h->stage2d_rows;
+    launch(h, K_STAGE1, [&] { lw::launch_stage2d<1>(af, af.c, af.c1, H, s); });
+    launch(h, K_STAGE2, [&] { lw::launch_stage2d<2>(af, af.c1, af.c2, H, s); });
+    launch(h, K_STAGE3, [&] { lw::launch_stage2d<3>(af, af.c2, af.c, H, s); });  // + deposit
+    return;
+  }
   if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d) {
     const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
     const int H = h->sweep3d_rows;
@@ -310,6 +321,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
 
 int launches_per_step(const lbm_wenoc* h) {
   if (h->sweep) return h->frozen ? 1 : 2;
+  if (h->stage2d) return (h->frozen ? 0 : 1) + 3;
   return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0);
 }
 
@@ -392,7 +404,15 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : p->settling_velocity + h->p.u_cap;
   cudaGetDevice(&h->device);
-  h->sweep = !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls);
+  h->sweep = !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
+             (p->flags & LW_FUSED_RK3) != 0;
+  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
+               (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
+  if (h->stage2d) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
+    h->stage2d_rows = lw::stage2d_rows(p->nx, p->ny, sms, 0);
+  }
   if (h->sweep) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
@@ -612,12 +632,13 @@ int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, in
 
 int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows) {
   if (!h || rows < 0) return LW_EINVAL;
-  if (h->sweep3d) {
+  if (h->sweep3d || h->stage2d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
     destroy_graphs(h);
-    h->sweep3d_rows = lw::sweep3d_rows(h->p.nx, h->p.ny, h->p.nz, sms, rows);
+    if (h->sweep3d) h->sweep3d_rows = lw::sweep3d_rows(h->p.nx, h->p.ny, h->p.nz, sms, rows);
+    if (h->stage2d) h->stage2d_rows = lw::stage2d_rows(h->p.nx, h->p.ny, sms, rows);
     return LW_OK;
   }
   if (!h->sweep) return LW_OK;

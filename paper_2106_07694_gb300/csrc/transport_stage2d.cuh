@@ -1,0 +1,217 @@
+// 2D FP32 transport: one SSP-RK3 stage of the WENO5 + diffusion + settling update of c
+// (steps a4..a8) as a row sweep, the 2D counterpart of the 3D stage kernels.
+//
+// A CTA owns a strip of 128 columns and a segment of rows and sweeps it upward.  At row
+// k it stages the x-split fluxes of the stage input on the strip plus a 3-column halo
+// in shared memory (prefetched one row ahead), computes the left x face of every column
+// (the strip's right edge face by one lane of warp 0), and the upper y face of its own
+// column from a ring of y-split fluxes running three rows ahead; the lower y face is
+// carried from the previous row.  Every face of the stage is computed once.  Small
+// shared-memory footprint (about 14 KB), so many CTAs share an SM.  Three launches make
+// a step (the stage-3 kernel also folds the floor deposit); c1 and c2 go through L2/HBM.
+#pragma once
+#include "common.cuh"
+#include "transport_sweep2d.cuh"  // weno5_face_value, face_flux_x
+
+namespace lw {
+
+constexpr int kS2T = 128;             // columns per CTA (threads)
+constexpr int kS2h = 3;               // stencil radius
+constexpr int kS2X = kS2T + 2 * kS2h;
+constexpr int kS2r = 8;               // y ring depth
+
+struct Stage2dSmem {
+  float xp[kS2X];  // x-split h+/alpha of the current row (strip + halo)
+  float xm[kS2X];
+  float c[kS2X];   // stage input value of the current row
+  float yp[kS2r][kS2T];  // y-split ring of each column
+  float ym[kS2r][kS2T];
+  float cy[kS2r][kS2T];  // stage input value ring of each column
+  float fx[kS2T + 1];    // left x faces (+ right edge)
+};
+
+struct Stage2dParams {
+  const float* cin;  // stage input (c, c1 or c2)
+  float* cout;       // stage output (c1, c2 or c in place)
+  int H;             // rows per segment
+};
+
+template <int STAGE>
+__global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2dParams sp) {
+  __shared__ __align__(16) Stage2dSmem S;
+  const int t = threadIdx.x;
+  const int nx = a.nx, ny = a.ny;
+  const int x0 = blockIdx.x * kS2T;
+  const int y0 = blockIdx.y * sp.H, y1 = min(ny, y0 + sp.H);
+  const int X = (x0 + t) % nx;
+  const bool out = x0 + t < nx;
+  const float inv_alpha = a.inv_alpha, vs_a = a.vs * a.inv_alpha, alpha = a.alpha, kappa = a.kappa;
+  const float* __restrict__ cin = sp.cin;
+  const float* __restrict__ ux = a.u;
+  const float* __restrict__ uy = a.u + a.n;
+
+  // staging positions of this thread in the strip + halo row (fixed for the sweep)
+  const int j1 = t + kS2T;  // second position, only for the 6 halo columns
+  const unsigned gx1 = (unsigned)((x0 - kS2h + j1 + 4 * nx) % nx);
+  const unsigned gxs = (unsigned)((x0 - kS2h + t + 4 * nx) % nx);
+  const bool has2 = j1 < kS2X;
+  float p0c = 0.f, p0u = 0.f, p1c = 0.f, p1u = 0.f;
+  auto fetch_row = [&](int k) {
+    if (k >= y1) return;
+    const unsigned row = (unsigned)k * (unsigned)nx;
+    p0c = __ldg(cin + row + gxs);
+    p0u = __ldg(ux + row + gxs);
+    if (has2) {
+      p1c = __ldg(cin + row + gx1);
+      p1u = __ldg(ux + row + gx1);
+    }
+  };
+  // own column, row l (ghost rows reflect): value and scaled vertical velocity
+  float qc = 0.f, qw = 0.f, qn = 0.f;
+  auto col_fetch = [&](int l) {
+    const bool ghost = l < 0 || l >= ny;
+    const int lr = l < 0 ? -1 - l : (l >= ny ? 2 * ny - 1 - l : l);
+    const unsigned k = (unsigned)lr * (unsigned)nx + X;
+    qc = __ldg(cin + k);
+    const float u = __ldg(uy + k);
+    qw = fmaf(ghost ? -u : u, inv_alpha, -vs_a);
+  };
+  auto col_put = [&](int l) {
+    const float h = 0.5f * qc;
+    S.yp[l & (kS2r - 1)][t] = fmaf(qw, h, h);
+    S.ym[l & (kS2r - 1)][t] = fmaf(qw, h, -h);
+    S.cy[l & (kS2r - 1)][t] = qc;
+  };
+  auto cn_fetch = [&](int k) {
+    if (STAGE > 1 && k < y1) qn = a.c[(unsigned)k * (unsigned)nx + X];
+  };
+
+  const int kb = y0 == 0 ? 0 : y0 - 1;  // first row: y0, or the priming row below it
+  for (int l = kb - 2; l < kb + 3; ++l) {
+    col_fetch(l);
+    col_put(l);
+  }
+  col_fetch(kb + 3);
+  fetch_row(kb);
+  cn_fetch(kb);
+  float carry = 0.f;
+  double dep = 0.0;  // stage 3, floor row: this column's Vs-free deposit term
+
+  for (int k = kb; k < y1; ++k) {
+    const bool prime = k < y0;
+    // ---- stage row k (prefetched), own column three rows ahead
+    {
+      const float h0 = 0.5f * p0c, w0 = p0u * inv_alpha;
+      S.c[t] = p0c;
+      S.xp[t] = fmaf(w0, h0, h0);
+      S.xm[t] = fmaf(w0, h0, -h0);
+      if (has2) {
+        const float h1 = 0.5f * p1c, w1 = p1u * inv_alpha;
+        S.c[j1] = p1c;
+        S.xp[j1] = fmaf(w1, h1, h1);
+        S.xm[j1] = fmaf(w1, h1, -h1);
+      }
+    }
+    fetch_row(k + 1);
+    col_put(k + 3);
+    col_fetch(k + 4);
+    const float cn_here = qn;
+    cn_fetch(k + 1);
+    __syncthreads();
+
+    // ---- faces: left x face of this column (and the strip's right edge), upper y face
+    if (!prime) {
+      S.fx[t] = face_flux_x(S.xp[t], S.xp[t + 1], S.xp[t + 2], S.xp[t + 3], S.xp[t + 4], S.xm[t + 5], S.xm[t + 4],
+                            S.xm[t + 3], S.xm[t + 2], S.xm[t + 1], alpha, kappa, S.c[t + kS2h - 1], S.c[t + kS2h]);
+      if (t == 0) {
+        const int e = kS2T;
+        S.fx[e] = face_flux_x(S.xp[e], S.xp[e + 1], S.xp[e + 2], S.xp[e + 3], S.xp[e + 4], S.xm[e + 5], S.xm[e + 4],
+                              S.xm[e + 3], S.xm[e + 2], S.xm[e + 1], alpha, kappa, S.c[e + kS2h - 1], S.c[e + kS2h]);
+      }
+    }
+    const float chere = S.cy[k & (kS2r - 1)][t];
+    float fup = 0.f;
+    if (k != ny - 1) {
+      fup = face_flux_x(S.yp[(k - 2) & (kS2r - 1)][t], S.yp[(k - 1) & (kS2r - 1)][t], S.yp[k & (kS2r - 1)][t],
+                        S.yp[(k + 1) & (kS2r - 1)][t], S.yp[(k + 2) & (kS2r - 1)][t], S.ym[(k + 3) & (kS2r - 1)][t],
+                        S.ym[(k + 2) & (kS2r - 1)][t], S.ym[(k + 1) & (kS2r - 1)][t], S.ym[k & (kS2r - 1)][t],
+                        S.ym[(k - 1) & (kS2r - 1)][t], alpha, kappa, chere, S.cy[(k + 1) & (kS2r - 1)][t]);
+    }
+    __syncthreads();
+
+    // ---- divergence and the Shu-Osher combination of this stage
+    if (!prime) {
+      const float fdn = k == 0 ? -a.vs * chere : carry;
+      const float L = S.fx[t] - S.fx[t + 1] + fdn - fup;
+      if (out) {
+        float v;
+        if (STAGE == 1) {
+          v = chere + L;
+        } else if (STAGE == 2) {
+          v = fmaf(0.75f, cn_here, 0.25f * (chere + L));
+        } else {
+          const float s = chere + L;
+          v = fmaf(1.f / 3.f, cn_here - s, s);
+        }
+        sp.cout[(unsigned)k * (unsigned)nx + X] = v;
+        if (STAGE == 3) {
+          report_status(a.status, !isfinite(v));
+          if (k == 0)  // RK3 b-weights of the floor flux: c^n/6 + c1/6 + 2 c2/3
+            dep = ((double)cn_here + (double)a.c1[X]) * (1.0 / 6.0) + (double)chere * (2.0 / 3.0);
+        }
+      }
+    }
+    carry = fup;
+  }
+
+  // stage 3: the CTAs holding the floor row fold the deposit of this step (FP64,
+  // fixed order: warp shuffles, then the last CTA sums the per-CTA partials)
+  if (STAGE == 3 && y0 == 0) {
+    __shared__ double red[kS2T / 32];
+    __shared__ bool last;
+    double v = dep;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) red[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+      double s2 = 0.0;
+      for (int w = 0; w < kS2T / 32; ++w) s2 += red[w];
+      a.partials[blockIdx.x] = s2 * (double)a.vs;
+      __threadfence();
+      last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && t == 0) {
+      __threadfence();
+      const volatile double* vp = a.partials;
+      double tot = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) tot += vp[b];
+      a.scalars[0] += tot;
+      *a.ticket = 0u;
+    }
+  }
+}
+
+inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
+  if (override_rows > 0) return min(override_rows, ny);
+  const long long strips = (nx + kS2T - 1) / kS2T;
+  // many short segments balance best (measured on the 2048 x 4096 lattice: 16 rows);
+  // fewer, longer ones when the lattice is small
+  long long segs = (27LL * sm_count + strips - 1) / strips;
+  int H = (int)((ny + segs - 1) / segs);
+  return max(min(16, ny), H);
+}
+
+template <int STAGE>
+inline cudaError_t launch_stage2d(const Args<float>& a, const float* cin, float* cout, int H, cudaStream_t s) {
+  Stage2dParams sp;
+  sp.cin = cin;
+  sp.cout = cout;
+  sp.H = H;
+  const dim3 grid((a.nx + kS2T - 1) / kS2T, (a.ny + H - 1) / H);
+  rk_stage2d_kernel<STAGE><<<grid, kS2T, 0, s>>>(a, sp);
+  return cudaGetLastError();
+}
+
+}  // namespace lw

@@ -30,6 +30,8 @@
 #include "common.cuh"
 #include "reduce_kernels.cuh"
 
+#include <type_traits>
+
 namespace lw {
 
 // ---------------------------------------------------------------- WENO5-JS, scalar FP32
@@ -192,7 +194,10 @@ __global__ void __launch_bounds__(kSwThreads, 2) rk3_sweep2d_kernel(Args<float> 
   const int r_end = hi3 - 1 + 9;
 
   // input rows prefetched three rows ahead (ghost rows reflect into the fluid)
-  float qc[3] = {0.f, 0.f, 0.f}, qx[3] = {0.f, 0.f, 0.f}, qy[3] = {0.f, 0.f, 0.f};
+  // Two register sets, used alternately by the even and odd iterations of the unrolled
+  // loop: the loads of row r0 + 2 go into the set row r0 has just released, so a load
+  // has two iterations to land and no register is moved while it is in flight.
+  float qc[2] = {0.f, 0.f}, qx[2] = {0.f, 0.f}, qy[2] = {0.f, 0.f};
   auto fetch = [&](int r, float& c, float& vx, float& vy) {
     if (r > r_load_end) return;
     const int rr = r < 0 ? -1 - r : (r >= ny ? 2 * ny - 1 - r : r);
@@ -203,14 +208,13 @@ __global__ void __launch_bounds__(kSwThreads, 2) rk3_sweep2d_kernel(Args<float> 
   };
   fetch(r_begin, qc[0], qx[0], qy[0]);
   fetch(r_begin + 1, qc[1], qx[1], qy[1]);
-  fetch(r_begin + 2, qc[2], qx[2], qy[2]);
 
   float carry[3] = {0.f, 0.f, 0.f};
   float dep_c = 0.f, dep_c1 = 0.f, dep_c2 = 0.f;  // floor values (this column) for the deposit
   int sy = ((r_begin % kRy) + kRy) % kRy;         // y-ring slot of row r0
 
-  for (int r0 = r_begin; r0 <= r_end; ++r0) {
-    const int par = r0 & 1;
+  auto body = [&](auto P, const int r0) {
+    constexpr int par = decltype(P)::value;  // register set and fx buffer of this iteration
     const int r1 = r0 - 3, r2 = r0 - 6, r3 = r0 - 9;
     const bool act1 = r1 >= lo1 && r1 < hi1, act2 = r2 >= lo2 && r2 < hi2, act3 = r3 >= lo3 && r3 < hi3;
     const bool prime1 = lo1 > 0 && r1 == lo1 - 1, prime2 = lo2 > 0 && r2 == lo2 - 1, prime3 = lo3 > 0 && r3 == lo3 - 1;
@@ -234,10 +238,8 @@ __global__ void __launch_bounds__(kSwThreads, 2) rk3_sweep2d_kernel(Args<float> 
     if (act2) S.fx[par][1][kSwPad + t] = xface(S, 1, S.c1[r2 & (kRc - 1)], r2, t, alpha, kappa);
     if (act3) S.fx[par][2][kSwPad + t] = xface(S, 2, S.c2[r3 & (kRc - 1)], r3, t, alpha, kappa);
     if (r0 <= r_load_end) {
-      const float c = qc[0], vx = qx[0], vy = qy[0];
-      qc[0] = qc[1]; qx[0] = qx[1]; qy[0] = qy[1];
-      qc[1] = qc[2]; qx[1] = qx[2]; qy[1] = qy[2];
-      fetch(r0 + 3, qc[2], qx[2], qy[2]);
+      const float c = qc[par], vx = qx[par], vy = qy[par];
+      fetch(r0 + 2, qc[par], qx[par], qy[par]);
       if (r0 >= 0 && r0 < ny) {
         const float wx = vx * inv_alpha;
         const float wy = fmaf(vy, inv_alpha, -vs_a);
@@ -316,6 +318,10 @@ __global__ void __launch_bounds__(kSwThreads, 2) rk3_sweep2d_kernel(Args<float> 
       carry[2] = fup;
     }
     sy = sy == kRy - 1 ? 0 : sy + 1;
+  };
+  for (int r0 = r_begin; r0 <= r_end; r0 += 2) {
+    body(std::integral_constant<int, 0>(), r0);
+    if (r0 + 1 <= r_end) body(std::integral_constant<int, 1>(), r0 + 1);
   }
 
   // ---- deposit of this step: Vs * sum over the floor of c/6 + c1/6 + 2 c2/3, in FP64;

@@ -25,6 +25,7 @@ LW_FP64 = 0x1
 LW_PERIODIC_VERTICAL = 0x2
 LW_FROZEN_VELOCITY = 0x4
 LW_NO_GRAPH = 0x8
+LW_FUSED_RK3 = 0x10
 
 _ERRORS = {LW_EINVAL: "LW_EINVAL", LW_ENOMEM: "LW_ENOMEM", LW_ECUDA: "LW_ECUDA",
            LW_EUNSTABLE: "LW_EUNSTABLE", LW_ETIMEOUT: "LW_ETIMEOUT", LW_ESTATE: "LW_ESTATE"}
@@ -210,7 +211,7 @@ def lbm_wenoc_destroy(h):
 
 def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0,
                 diffusivity=0.0, lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), fp64=False,
-                periodic_vertical=False, frozen_velocity=False, graphs=True):
+                periodic_vertical=False, frozen_velocity=False, graphs=True, fused_rk3=False):
     p = lbm_wenoc_params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -220,7 +221,8 @@ def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velo
     for d in range(3):
         p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
     p.flags = ((LW_FP64 if fp64 else 0) | (LW_PERIODIC_VERTICAL if periodic_vertical else 0) |
-               (LW_FROZEN_VELOCITY if frozen_velocity else 0) | (0 if graphs else LW_NO_GRAPH))
+               (LW_FROZEN_VELOCITY if frozen_velocity else 0) | (0 if graphs else LW_NO_GRAPH) |
+               (LW_FUSED_RK3 if fused_rk3 else 0))
     return p
 
 

@@ -24,9 +24,9 @@ def _lib():
     build.build()
 
 
-def _pair(shape, c0, u0=None, fp64=True, **kw):
+def _pair(shape, c0, u0=None, fp64=True, fused_rk3=False, **kw):
     from paper_2106_07694_gb300.lbm_wenoc import Simulation
-    g = Simulation(shape, fp64=fp64, **kw)
+    g = Simulation(shape, fp64=fp64, fused_rk3=fused_rk3, **kw)
     if not fp64:
         c0 = c0.astype(np.float32).astype(np.float64)
         if u0 is not None:
@@ -121,12 +121,13 @@ def test_fp64_frozen_velocity_with_walls():
 
 # ------------------------------------------------------------------ FP32
 
-def test_fp32_small_workload_before_saturation():
+@pytest.mark.parametrize("fused", [False, True])
+def test_fp32_small_workload_before_saturation(fused):
     wl = workloads.SMALL_2D
     c0 = wl.initial_c()
     kw = dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
               settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity)
-    g, o = _pair(wl.shape, c0, fp64=False, **kw)
+    g, o = _pair(wl.shape, c0, fp64=False, fused_rk3=fused, **kw)
     for n in (1, 1, 98, 200):
         g.step(n)
         o.step(n)
@@ -136,28 +137,31 @@ def test_fp32_small_workload_before_saturation():
     assert abs(g.deposit - o.deposit) <= 1e-5 * abs(o.deposit)
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("shape", [(132, 40), (260, 70), (4, 8)])
-def test_fp32_ragged_shapes_frozen_velocity(shape):
+def test_fp32_ragged_shapes_frozen_velocity(shape, fused):
     rng = np.random.default_rng(shape[0])
     nx, ny = shape
     c0 = rng.uniform(0, 1, size=(ny, nx))
     u0 = rng.uniform(-0.05, 0.05, size=(2, ny, nx))
     kw = dict(settling_velocity=2e-3, diffusivity=1e-3, frozen_velocity=True)
-    g, o = _pair(shape, c0, u0, fp64=False, **kw)
+    g, o = _pair(shape, c0, u0, fp64=False, fused_rk3=fused, **kw)
     g.step(3)
     o.step(3)
     _compare(g, o, 2e-6, 1e-7, 0.0)
     assert abs(g.deposit - o.deposit) <= 1e-5 * abs(o.deposit)
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("shape", [(128, 70), (500, 37)])
-def test_fp32_sweep_segments_are_bitwise_invariant(shape):
-    # The fused 2D FP32 transport splits rows into CTA segments with primed stage
-    # pipelines; any segment height must give the same bits as the default.
+def test_fp32_sweep_segments_are_bitwise_invariant(shape, fused):
+    # The 2D FP32 transport (three row-sweep stage kernels, or the fused sweep) splits
+    # rows into CTA segments with primed pipelines; any segment height must give the same
+    # bits as the default.
     from paper_2106_07694_gb300 import lbm_wenoc as lw
     from paper_2106_07694_gb300.lbm_wenoc import Simulation
     c0 = workloads.interface_field(shape, amplitude=0.05, seed=9)
-    kw = dict(PHYS, gravity=5e-4, settling_velocity=3e-3)
+    kw = dict(PHYS, gravity=5e-4, settling_velocity=3e-3, fused_rk3=fused)
     ref = Simulation(shape, fp64=False, **kw)
     ref.init(c0)
     ref.step(6)
@@ -171,7 +175,8 @@ def test_fp32_sweep_segments_are_bitwise_invariant(shape):
         for g_, w_ in zip(got, want):
             assert np.array_equal(g_, w_), rows
         assert s.deposit == ref.deposit
-    o = oracle.OracleSim(shape, **kw)
+    kwo = {k: v for k, v in kw.items() if k != "fused_rk3"}
+    o = oracle.OracleSim(shape, **kwo)
     o.init(c0.astype(np.float32).astype(np.float64))
     o.step(6)
     assert rel_l2(want[2], o.fields()[2]) < 1e-6
