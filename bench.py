@@ -105,7 +105,10 @@ class ClockSampler:
 # taken on; a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
     "rk3_sweep2d": (127.72e6, "paper_2106_07694_gb300/csrc/transport_sweep2d.cuh", "83e0464e30c5"),
-    "lbm_collide_stream": (646.51e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "b6edf2bfe444"),
+    "lbm_collide_stream": (645.79e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "3777e2a15a91"),
+    "rk_stage1": (116.03e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "d79897d5bdd3"),
+    "rk_stage2": (154.79e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "d79897d5bdd3"),
+    "rk_stage3": (149.83e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "d79897d5bdd3"),
 }
 
 
@@ -249,7 +252,7 @@ def bench_ours(args):
                "rk_stage2": tr_flop / 3, "rk_stage3": tr_flop / 3}
     sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
-    ncu_traffic = {k: kernel_traffic(k) if dim == 2 else None for k in ("rk3_sweep2d", "lbm_collide_stream")}
+    ncu_traffic = {k: kernel_traffic(k) if dim == 2 else None for k in NCU_TRAFFIC}
 
     def avg_s(name):
         n_, t_ = stats[name]
