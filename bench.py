@@ -31,6 +31,7 @@ WORKLOADS = {
     "3d": (workloads.MAIN_3D, "coupled LBM+WENO5 GLUPS (3D D3Q19 256x256x512 FP32)", "D3Q19"),
 }
 WL, METRIC, LATTICE = WORKLOADS["2d"]
+BATCH_METRIC = "coupled LBM+WENO5 GLUPS, batched sweep of 64 D2Q9 FP32 instances (256x512..1024x2048)"
 UNIT = "GLUPS"
 
 
@@ -341,6 +342,71 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def bench_batch(args):
+    """64 independent 2D instances (sizes and parameters of workloads.batch_sweep) advanced
+    by one launch per kernel type and step, against the same instances run one after the
+    other on the same GPU (each for the same number of steps)."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2106_07694_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    wls = workloads.batch_sweep(64)
+    specs = [dict(shape=w.shape, **phys_kwargs(w)) for w in wls]
+    nodes = sum(w.nodes for w in wls)
+    b = lw.Batch(specs)
+    rows = b.autotune(4)
+    for inst, w in zip(b.instances, wls):
+        inst.init(torch.from_numpy(w.initial_c().astype(np.float32)).cuda())
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = lw.lbm_wenoc_batch_launch_count(b.handle)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = lw.lbm_wenoc_batch_launch_count(b.handle) - l0
+    for inst in b.instances:
+        if inst.status() != lw.LW_OK:
+            raise RuntimeError("device status set in the batched run")
+    value = nodes * args.steps / (ms * 1e-3) / 1e9
+    b.close()
+    # sequential: the same instances one after the other, same number of steps each
+    seq_ms = 0.0
+    for w, sp in zip(wls, specs):
+        s = lw.Simulation(w.shape, **{k: v for k, v in sp.items() if k != "shape"})
+        s.init(torch.from_numpy(w.initial_c().astype(np.float32)).cuda())
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record()
+        s.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        s.close()
+    seq = nodes * args.steps / (seq_ms * 1e-3) / 1e9
+    peak, _ = load_peaks()
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch_sweep_64_d2q9_f32", "instances": len(wls), "nodes": nodes,
+                   "autotuned_segment_rows": rows, "seed": 0},
+        "sequential": {"value": seq, "unit": UNIT, "ms_per_step": seq_ms / args.steps,
+                       "note": "each instance alone through lbm_wenoc_step, one after the other"},
+        "batched_over_sequential": value / seq,
+        "step_roofline": {"bound": "hbm", "alg_bytes_per_node": 80, "achieved": 80 * value, "peak": peak,
+                          "unit": "GB/s", "frac": 80 * value / peak},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,10 +415,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS),
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batch"],
                     help="2d: the 2048x4096 D2Q9 case the metric is quoted on; 3d: 256x256x512 D3Q19")
     args = ap.parse_args()
     global WL, METRIC, LATTICE
+    if args.workload == "batch":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched sweep has no oracle arm; "
+                              "the oracle is timed on the single-instance workloads"}))
+            return
+        bench_batch(args)
+        return
     WL, METRIC, LATTICE = WORKLOADS[args.workload]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -136,6 +136,40 @@ int64_t lbm_wenoc_launch_count(const lbm_wenoc* h);
  * captured graphs; call between steps. */
 int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows);
 
+/* ---- Batched simulations (the paper's parameter sweep, Sec. 2.2 Table 1, as one job) ----
+ * count independent 2D FP32 simulations with walls (no LW_FP64, LW_PERIODIC_VERTICAL,
+ * LW_FROZEN_VELOCITY or LW_FUSED_RK3), each with its own size and parameters, in one
+ * caller-owned workspace, advanced together by one launch per kernel type and step. */
+typedef struct lbm_wenoc_batch lbm_wenoc_batch;
+
+/* Workspace bytes for count instances with parameters p[0..count); LW_EINVAL if any
+ * instance is not a 2D FP32 walled configuration. */
+int lbm_wenoc_batch_workspace_bytes(const lbm_wenoc_params* p, int32_t count, size_t* bytes);
+
+/* Create the batch over dev_workspace (256-byte aligned, at least the bytes above). */
+int lbm_wenoc_batch_create(const lbm_wenoc_params* p, int32_t count, void* dev_workspace, size_t bytes,
+                           void* cuda_stream, lbm_wenoc_batch** out);
+
+/* Handle of instance i (owned by the batch: do not destroy it).  Use it for init,
+ * fields, deposited_mass, total_mass and status; stepping it alone desynchronises it
+ * from the batch (lbm_wenoc_batch_step then returns LW_ESTATE). */
+lbm_wenoc* lbm_wenoc_batch_instance(lbm_wenoc_batch* b, int32_t i);
+
+/* Advance every instance nsteps steps (asynchronous); all instances must be
+ * initialised and at the same step count, else LW_ESTATE. */
+int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps);
+
+/* Autotuner: times steps_per_trial batched steps for each candidate segment height of
+ * the transport kernels (8, 16, 32, 64 rows) on a trial state, keeps the fastest and
+ * returns it in *chosen_rows.  Leaves every instance uninitialised: call it before init. */
+int lbm_wenoc_batch_autotune(lbm_wenoc_batch* b, int32_t steps_per_trial, int32_t* chosen_rows);
+
+/* Kernel launches issued by lbm_wenoc_batch_step so far. */
+int64_t lbm_wenoc_batch_launch_count(const lbm_wenoc_batch* b);
+
+/* Destroy the batch and its instance handles (not the caller's workspace). */
+void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b);
+
 /* Sum of a concentration field, FP64, for callers that cannot allocate device memory
  * (an application that owns a fixed device arena, a plugin inside another framework's
  * allocator, a tool holding only a pointer to someone else's field).  The paper has no

@@ -90,7 +90,7 @@ class OracleSim:
     (numpy shape (ny, nx) or (nz, ny, nx)); the vertical axis is the slowest one.
     """
 
-    def __init__(self, shape, tau=0.6, gravity=1.0, density_contrast=0.0,
+    def __init__(self, shape, tau=0.6, gravity=0.0, density_contrast=1.0,
                  settling_velocity=0.0, diffusivity=0.0, lf_alpha=0.0, u_cap=0.0,
                  body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False):
         dim = len(shape)

@@ -146,9 +146,18 @@ __global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
 // hints on the population traffic (each population is touched once per step), so
 // that c and u stay in L2 for the transport kernel that follows.
 template <typename T, int PARITY>
+__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by);
+
+template <typename T, int PARITY>
 __global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
+  lbm_d2q9_body<T, PARITY>(a, blockIdx.x, blockIdx.y);
+}
+
+// Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.
+template <typename T, int PARITY>
+__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by) {
+  const int x = bx * blockDim.x + threadIdx.x;
+  const int y = by;
   const int nx = a.nx, ny = a.ny;
   if (x >= nx) return;
   const unsigned n = (unsigned)a.n;

@@ -21,6 +21,7 @@
 #include "transport_sweep2d.cuh"
 #include "transport_sweep3d.cuh"
 #include "transport_stage2d.cuh"
+#include "batch.cuh"
 
 namespace {
 
@@ -657,6 +658,271 @@ void lbm_wenoc_destroy(lbm_wenoc* h) {
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   destroy_graphs(h);
   delete h;
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Batched simulations: one handle per instance over consecutive slices of one
+// workspace, plus device tables, advanced together by one launch per kernel type.
+
+struct lbm_wenoc_batch {
+  std::vector<lbm_wenoc*> inst;
+  std::vector<size_t> offsets;  // workspace offset of each instance
+  unsigned char* ws = nullptr;
+  size_t tables_off = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int rows = 0;  // segment rows of the stage kernels (0: per-instance default)
+  int lbm_blocks = 0, st_blocks = 0;
+  lw::BatchTables tab{};
+  static constexpr int kGraphSteps = 16;
+  cudaGraphExec_t graph_many[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_one[2] = {nullptr, nullptr};
+  int64_t launches = 0;
+};
+
+namespace {
+
+bool batch_params_ok(const lbm_wenoc_params& p) {
+  return check_params(&p) == LW_OK && p.dim == 2 && !(p.flags & LW_FP64) && !(p.flags & LW_PERIODIC_VERTICAL) &&
+         !(p.flags & LW_FROZEN_VELOCITY) && !(p.flags & LW_FUSED_RK3) &&
+         (p.nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
+}
+
+size_t batch_tables_bytes(int count) {
+  return align_up(sizeof(Args<float>) * count, 256) + align_up(sizeof(int) * (count + 1), 256) * 2 +
+         align_up(sizeof(int) * count, 256) * 3;
+}
+
+void batch_destroy_graphs(lbm_wenoc_batch* b) {
+  for (int i = 0; i < 2; ++i) {
+    if (b->graph_many[i]) cudaGraphExecDestroy(b->graph_many[i]);
+    if (b->graph_one[i]) cudaGraphExecDestroy(b->graph_one[i]);
+    b->graph_many[i] = b->graph_one[i] = nullptr;
+  }
+}
+
+// Fill the device tables from the instances' current argument blocks and geometries.
+int batch_upload_tables(lbm_wenoc_batch* b) {
+  const int count = (int)b->inst.size();
+  std::vector<Args<float>> args(count);
+  std::vector<int> lstart(count + 1), lgx(count), sstart(count + 1), sstrips(count), srows(count);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || sms <= 0) sms = 148;
+  lstart[0] = sstart[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    lbm_wenoc* h = b->inst[i];
+    args[i] = make_args<float>(h);
+    lgx[i] = (h->p.nx + kLbmThreads - 1) / kLbmThreads;
+    lstart[i + 1] = lstart[i] + lgx[i] * h->p.ny;
+    sstrips[i] = (h->p.nx + lw::kS2T - 1) / lw::kS2T;
+    srows[i] = b->rows > 0 ? std::min(b->rows, h->p.ny) : h->stage2d_rows;
+    const int segs = (h->p.ny + srows[i] - 1) / srows[i];
+    sstart[i + 1] = sstart[i] + sstrips[i] * segs;
+  }
+  b->lbm_blocks = lstart[count];
+  b->st_blocks = sstart[count];
+  unsigned char* base = b->ws + b->tables_off;
+  size_t off = 0;
+  auto put = [&](const void* src, size_t nbytes) -> const void* {
+    unsigned char* dst = base + off;
+    off += align_up(nbytes, 256);
+    if (cudaMemcpyAsync(dst, src, nbytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) return nullptr;
+    return dst;
+  };
+  b->tab.args = static_cast<const Args<float>*>(put(args.data(), sizeof(Args<float>) * count));
+  b->tab.lbm_start = static_cast<const int*>(put(lstart.data(), sizeof(int) * (count + 1)));
+  b->tab.st_start = static_cast<const int*>(put(sstart.data(), sizeof(int) * (count + 1)));
+  b->tab.lbm_gx = static_cast<const int*>(put(lgx.data(), sizeof(int) * count));
+  b->tab.st_strips = static_cast<const int*>(put(sstrips.data(), sizeof(int) * count));
+  b->tab.st_rows = static_cast<const int*>(put(srows.data(), sizeof(int) * count));
+  b->tab.count = count;
+  if (!b->tab.args || !b->tab.lbm_start || !b->tab.st_start || !b->tab.lbm_gx || !b->tab.st_strips || !b->tab.st_rows)
+    return LW_ECUDA;
+  // the host vectors go out of scope: wait for the copies
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LW_ECUDA;
+  batch_destroy_graphs(b);
+  return LW_OK;
+}
+
+void batch_enqueue(lbm_wenoc_batch* b, cudaStream_t s, int parity) {
+  const lw::BatchTables t = b->tab;
+  if (parity == 0)
+    lw::lbm_d2q9_batch_kernel<0><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
+  else
+    lw::lbm_d2q9_batch_kernel<1><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
+  lw::stage2d_batch_kernel<1><<<b->st_blocks, lw::kS2T, 0, s>>>(t);
+  lw::stage2d_batch_kernel<2><<<b->st_blocks, lw::kS2T, 0, s>>>(t);
+  lw::stage2d_batch_kernel<3><<<b->st_blocks, lw::kS2T, 0, s>>>(t);
+}
+
+int batch_capture(lbm_wenoc_batch* b, int parity, int count, cudaGraphExec_t* out) {
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LW_ECUDA;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < count; ++k) batch_enqueue(b, cap, (parity + k) & 1);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  return e == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+// Advance every instance; requires equal step counts (shared AA parity).
+int batch_advance(lbm_wenoc_batch* b, int64_t nsteps, bool require_init) {
+  if (nsteps < 0) return LW_EINVAL;
+  const int par = b->inst[0]->parity;
+  for (lbm_wenoc* h : b->inst) {
+    if (require_init && !h->initialised) return LW_ESTATE;
+    if (h->parity != par || h->steps != b->inst[0]->steps) return LW_ESTATE;
+  }
+  int64_t left = nsteps;
+  int parity = par;
+  while (left > 0) {
+    const bool many = left >= lbm_wenoc_batch::kGraphSteps;
+    cudaGraphExec_t* slot = many ? &b->graph_many[parity] : &b->graph_one[parity];
+    const int count = many ? lbm_wenoc_batch::kGraphSteps : 1;
+    if (!*slot) {
+      int rc = batch_capture(b, parity, count, slot);
+      if (rc != LW_OK) return rc;
+    }
+    if (cudaGraphLaunch(*slot, b->stream) != cudaSuccess) return LW_ECUDA;
+    b->launches += 4LL * count;
+    parity = (parity + count) & 1;
+    left -= count;
+  }
+  for (lbm_wenoc* h : b->inst) {
+    h->parity = parity;
+    h->steps += nsteps;
+    h->launches += 4 * nsteps;
+  }
+  return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_wenoc_batch_workspace_bytes(const lbm_wenoc_params* p, int32_t count, size_t* bytes) {
+  if (!p || !bytes || count < 1) return LW_EINVAL;
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!batch_params_ok(p[i])) return LW_EINVAL;
+    total += align_up(make_layout(p[i]).total, 256);
+  }
+  *bytes = total + batch_tables_bytes(count);
+  return LW_OK;
+}
+
+int lbm_wenoc_batch_create(const lbm_wenoc_params* p, int32_t count, void* dev_workspace, size_t bytes,
+                           void* cuda_stream, lbm_wenoc_batch** out) {
+  if (!out) return LW_EINVAL;
+  *out = nullptr;
+  size_t need = 0;
+  int rc = lbm_wenoc_batch_workspace_bytes(p, count, &need);
+  if (rc != LW_OK) return rc;
+  if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255u) != 0) return LW_EINVAL;
+  if (bytes < need) return LW_ENOMEM;
+  lbm_wenoc_batch* b = new (std::nothrow) lbm_wenoc_batch();
+  if (!b) return LW_ENOMEM;
+  b->ws = static_cast<unsigned char*>(dev_workspace);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&b->device);
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    const size_t sz = align_up(make_layout(p[i]).total, 256);
+    lbm_wenoc* h = nullptr;
+    rc = lbm_wenoc_create(&p[i], b->ws + off, sz, cuda_stream, &h);
+    if (rc != LW_OK || !h->stage2d) {
+      if (h) lbm_wenoc_destroy(h);
+      for (lbm_wenoc* q : b->inst) lbm_wenoc_destroy(q);
+      delete b;
+      return rc != LW_OK ? rc : LW_EINVAL;
+    }
+    b->inst.push_back(h);
+    b->offsets.push_back(off);
+    off += sz;
+  }
+  b->tables_off = off;
+  rc = batch_upload_tables(b);
+  if (rc != LW_OK) {
+    for (lbm_wenoc* q : b->inst) lbm_wenoc_destroy(q);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return LW_OK;
+}
+
+lbm_wenoc* lbm_wenoc_batch_instance(lbm_wenoc_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->inst.size()) return nullptr;
+  return b->inst[i];
+}
+
+int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps) {
+  if (!b) return LW_EINVAL;
+  return batch_advance(b, nsteps, true);
+}
+
+int lbm_wenoc_batch_autotune(lbm_wenoc_batch* b, int32_t steps_per_trial, int32_t* chosen_rows) {
+  if (!b || steps_per_trial < 1) return LW_EINVAL;
+  // trial state: c = 0 and the fluid at rest in every instance (the caller inits afterwards)
+  for (lbm_wenoc* h : b->inst) {
+    if (cudaMemsetAsync(h->ws + h->L.c, 0, (size_t)h->n * sizeof(float), b->stream) != cudaSuccess) return LW_ECUDA;
+    if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * 4, b->stream) != cudaSuccess) return LW_ECUDA;
+    if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, b->stream) != cudaSuccess) return LW_ECUDA;
+    h->cur = 0;
+    launch_init<D2Q9, float>(h, nullptr);
+    h->parity = 0;
+    h->steps = 0;
+  }
+  const int candidates[] = {8, 16, 32, 64};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LW_ECUDA;
+  int best = 0;
+  float best_ms = 0.f;
+  int rc = LW_OK;
+  for (int rows : candidates) {
+    b->rows = rows;
+    if ((rc = batch_upload_tables(b)) != LW_OK) break;
+    if ((rc = batch_advance(b, 1, false)) != LW_OK) break;  // warm-up (graph capture)
+    cudaEventRecord(e0, b->stream);
+    if ((rc = batch_advance(b, steps_per_trial, false)) != LW_OK) break;
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = LW_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best == 0 || ms < best_ms) {
+      best = rows;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LW_OK) return rc;
+  b->rows = best;
+  rc = batch_upload_tables(b);
+  for (lbm_wenoc* h : b->inst) h->initialised = false;  // trial state is not a user state
+  if (chosen_rows) *chosen_rows = best;
+  return rc;
+}
+
+int64_t lbm_wenoc_batch_launch_count(const lbm_wenoc_batch* b) { return b ? b->launches : -1; }
+
+void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_destroy_graphs(b);
+  for (lbm_wenoc* h : b->inst) lbm_wenoc_destroy(h);
+  delete b;
 }
 
 }  // extern "C"

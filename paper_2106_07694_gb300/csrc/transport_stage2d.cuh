@@ -36,13 +36,16 @@ struct Stage2dParams {
   int H;             // rows per segment
 };
 
+// Body of the stage kernel for strip bx, segment by; `strips` = number of strips (the
+// floor CTAs that fold the deposit).
 template <int STAGE>
-__global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2dParams sp) {
+__device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2dParams& sp, int bx, int by,
+                                             int strips) {
   __shared__ __align__(16) Stage2dSmem S;
   const int t = threadIdx.x;
   const int nx = a.nx, ny = a.ny;
-  const int x0 = blockIdx.x * kS2T;
-  const int y0 = blockIdx.y * sp.H, y1 = min(ny, y0 + sp.H);
+  const int x0 = bx * kS2T;
+  const int y0 = by * sp.H, y1 = min(ny, y0 + sp.H);
   const int X = (x0 + t) % nx;
   const bool out = x0 + t < nx;
   const float inv_alpha = a.inv_alpha, vs_a = a.vs * a.inv_alpha, alpha = a.alpha, kappa = a.kappa;
@@ -177,20 +180,25 @@ __global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2d
     if (t == 0) {
       double s2 = 0.0;
       for (int w = 0; w < kS2T / 32; ++w) s2 += red[w];
-      a.partials[blockIdx.x] = s2 * (double)a.vs;
+      a.partials[bx] = s2 * (double)a.vs;
       __threadfence();
-      last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+      last = atomicAdd(a.ticket, 1u) == (unsigned)strips - 1;
     }
     __syncthreads();
     if (last && t == 0) {
       __threadfence();
       const volatile double* vp = a.partials;
       double tot = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) tot += vp[b];
+      for (int b = 0; b < strips; ++b) tot += vp[b];
       a.scalars[0] += tot;
       *a.ticket = 0u;
     }
   }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2dParams sp) {
+  stage2d_body<STAGE>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {

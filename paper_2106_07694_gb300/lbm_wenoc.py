@@ -35,7 +35,9 @@ EXPORTED = [
     "lbm_wenoc_deposited_mass", "lbm_wenoc_total_mass", "lbm_wenoc_fields", "lbm_wenoc_status",
     "lbm_wenoc_steps", "lbm_wenoc_profile_enable", "lbm_wenoc_profile_read",
     "lbm_wenoc_launch_count", "lbm_wenoc_set_segment_rows", "lbm_wenoc_total_mass_noalloc",
-    "lbm_wenoc_destroy",
+    "lbm_wenoc_destroy", "lbm_wenoc_batch_workspace_bytes", "lbm_wenoc_batch_create",
+    "lbm_wenoc_batch_instance", "lbm_wenoc_batch_step", "lbm_wenoc_batch_autotune",
+    "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy",
 ]
 
 
@@ -104,8 +106,19 @@ def load():
     L.lbm_wenoc_total_mass_noalloc.argtypes = [vp, i64, ctypes.c_int32, vp, vp]
     L.lbm_wenoc_destroy.argtypes = [vp]
     L.lbm_wenoc_destroy.restype = None
+    L.lbm_wenoc_batch_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm_wenoc_batch_create.argtypes = [P, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.lbm_wenoc_batch_instance.argtypes = [vp, ctypes.c_int32]
+    L.lbm_wenoc_batch_instance.restype = vp
+    L.lbm_wenoc_batch_step.argtypes = [vp, i64]
+    L.lbm_wenoc_batch_autotune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    L.lbm_wenoc_batch_launch_count.argtypes = [vp]
+    L.lbm_wenoc_batch_launch_count.restype = i64
+    L.lbm_wenoc_batch_destroy.argtypes = [vp]
+    L.lbm_wenoc_batch_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("lbm_wenoc_steps", "lbm_wenoc_launch_count", "lbm_wenoc_destroy"):
+        if name not in ("lbm_wenoc_steps", "lbm_wenoc_launch_count", "lbm_wenoc_destroy",
+                        "lbm_wenoc_batch_instance", "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -298,3 +311,99 @@ class Simulation:
 
     def status(self):
         return lbm_wenoc_status(self.handle)
+
+
+# ---- batched simulations ---------------------------------------------------------------
+
+def lbm_wenoc_batch_workspace_bytes(params_list):
+    arr = (lbm_wenoc_params * len(params_list))(*params_list)
+    n = ctypes.c_size_t(0)
+    _check("lbm_wenoc_batch_workspace_bytes",
+           load().lbm_wenoc_batch_workspace_bytes(arr, len(params_list), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_wenoc_batch_create(params_list, workspace, nbytes, stream):
+    arr = (lbm_wenoc_params * len(params_list))(*params_list)
+    h = ctypes.c_void_p()
+    _check("lbm_wenoc_batch_create", load().lbm_wenoc_batch_create(arr, len(params_list), _ptr(workspace), nbytes,
+                                                                   stream, ctypes.byref(h)))
+    return h
+
+
+def lbm_wenoc_batch_instance(b, i):
+    return ctypes.c_void_p(load().lbm_wenoc_batch_instance(b, int(i)))
+
+
+def lbm_wenoc_batch_step(b, nsteps):
+    return _check("lbm_wenoc_batch_step", load().lbm_wenoc_batch_step(b, int(nsteps)))
+
+
+def lbm_wenoc_batch_autotune(b, steps_per_trial=4):
+    rows = ctypes.c_int32(0)
+    _check("lbm_wenoc_batch_autotune", load().lbm_wenoc_batch_autotune(b, int(steps_per_trial), ctypes.byref(rows)))
+    return rows.value
+
+
+def lbm_wenoc_batch_launch_count(b):
+    return load().lbm_wenoc_batch_launch_count(b)
+
+
+def lbm_wenoc_batch_destroy(b):
+    if b:
+        load().lbm_wenoc_batch_destroy(b)
+
+
+class _Instance:
+    """View of one instance of a Batch (same methods as Simulation, no own workspace)."""
+
+    def __init__(self, batch, i, shape, fp64=False):
+        import torch
+        self.handle = lbm_wenoc_batch_instance(batch.handle, i)
+        self.dim = len(shape)
+        self.grid = tuple(reversed([int(s) for s in shape]))
+        self.fp64 = fp64
+        self.dtype = torch.float32
+
+    init = Simulation.init
+    _as_input = Simulation._as_input
+    fields = Simulation.fields
+    deposit = Simulation.deposit
+    total_mass = Simulation.total_mass
+    steps = Simulation.steps
+    status = Simulation.status
+
+
+class Batch:
+    """Many 2D FP32 simulations (shapes and parameters per instance) advanced together.
+
+    specs: list of dicts with 'shape' and the keyword parameters of make_params."""
+
+    def __init__(self, specs, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbm_wenoc needs a CUDA device; there is no CPU fallback")
+        load()
+        self.params = [make_params(sp["shape"], **{k: v for k, v in sp.items() if k != "shape"}) for sp in specs]
+        nbytes = lbm_wenoc_batch_workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = lbm_wenoc_batch_create(self.params, self.workspace, nbytes, self.stream.cuda_stream)
+        self.instances = [_Instance(self, i, sp["shape"]) for i, sp in enumerate(specs)]
+
+    def autotune(self, steps_per_trial=4):
+        return lbm_wenoc_batch_autotune(self.handle, steps_per_trial)
+
+    def step(self, n=1):
+        lbm_wenoc_batch_step(self.handle, n)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_wenoc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
