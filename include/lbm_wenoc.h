@@ -170,6 +170,24 @@ int64_t lbm_wenoc_batch_launch_count(const lbm_wenoc_batch* b);
 /* Destroy the batch and its instance handles (not the caller's workspace). */
 void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b);
 
+/* ---- Gradient of the deposited mass (reverse mode, checkpoint-and-recompute) ----
+ * J = deposited mass (Sec. 4, m_b) after nsteps steps from the initial state c0 (fluid
+ * at rest).  lbm_wenoc_deposit_gradient runs the forward pass keeping the state every
+ * `segment` steps, then for each segment in reverse recomputes its states and runs the
+ * adjoint kernels backwards through every step (transport stages with the WENO5
+ * nonlinear weights, streaming with bounce-back, BGK-Guo collision, buoyancy), giving
+ *   grad_c0[n] = dJ/dc0   (caller buffer, host or device, element type of the handle)
+ *   *dJ_dVs     = dJ/dVs  (FP64; lf_alpha is held fixed)
+ *   *J          = the deposited mass of the forward pass (FP64).
+ * Requires a 2D handle with walls, not frozen, without LW_FUSED_RK3, and an explicit
+ * lf_alpha > 0 (LW_EINVAL otherwise).  adj_workspace: caller-owned device memory of at
+ * least lbm_wenoc_gradient_workspace_bytes() (checkpoints + one segment of states +
+ * adjoint fields), 256-byte aligned.  Synchronises.  Afterwards the handle holds an
+ * intermediate state and must be initialised again before stepping. */
+int lbm_wenoc_gradient_workspace_bytes(const lbm_wenoc_params* p, int64_t nsteps, int32_t segment, size_t* bytes);
+int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t segment, void* adj_workspace,
+                               size_t bytes, void* grad_c0, double* dJ_dVs, double* J);
+
 /* Sum of a concentration field, FP64, for callers that cannot allocate device memory
  * (an application that owns a fixed device arena, a plugin inside another framework's
  * allocator, a tool holding only a pointer to someone else's field).  The paper has no

@@ -38,6 +38,7 @@ EXPORTED = [
     "lbm_wenoc_destroy", "lbm_wenoc_batch_workspace_bytes", "lbm_wenoc_batch_create",
     "lbm_wenoc_batch_instance", "lbm_wenoc_batch_step", "lbm_wenoc_batch_autotune",
     "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy",
+    "lbm_wenoc_gradient_workspace_bytes", "lbm_wenoc_deposit_gradient",
 ]
 
 
@@ -116,6 +117,9 @@ def load():
     L.lbm_wenoc_batch_launch_count.restype = i64
     L.lbm_wenoc_batch_destroy.argtypes = [vp]
     L.lbm_wenoc_batch_destroy.restype = None
+    L.lbm_wenoc_gradient_workspace_bytes.argtypes = [P, i64, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.lbm_wenoc_deposit_gradient.argtypes = [vp, vp, i64, ctypes.c_int32, vp, ctypes.c_size_t, vp, dp, dp]
     for name in EXPORTED:
         if name not in ("lbm_wenoc_steps", "lbm_wenoc_launch_count", "lbm_wenoc_destroy",
                         "lbm_wenoc_batch_instance", "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy"):
@@ -215,6 +219,30 @@ def lbm_wenoc_total_mass_noalloc(c_dev, n, fp64, stream, out_dev):
                   load().lbm_wenoc_total_mass_noalloc(_ptr(c_dev), int(n), 1 if fp64 else 0, stream, _ptr(out_dev)))
 
 
+def lbm_wenoc_gradient_workspace_bytes(params, nsteps, segment):
+    n = ctypes.c_size_t(0)
+    _check("lbm_wenoc_gradient_workspace_bytes",
+           load().lbm_wenoc_gradient_workspace_bytes(ctypes.byref(params), int(nsteps), int(segment),
+                                                     ctypes.byref(n)))
+    return n.value
+
+
+def lbm_wenoc_deposit_gradient(h, c0, nsteps, segment, workspace, nbytes, grad_c0):
+    """Deposited mass J after nsteps steps from c0 and its gradient: writes dJ/dc0 into
+    grad_c0 and returns (J, dJ/dVs)."""
+    dvs = ctypes.c_double()
+    J = ctypes.c_double()
+    _check("lbm_wenoc_deposit_gradient",
+           load().lbm_wenoc_deposit_gradient(h, _ptr(c0), int(nsteps), int(segment), _ptr(workspace), nbytes,
+                                             _ptr(grad_c0), ctypes.byref(dvs), ctypes.byref(J)))
+    return J.value, dvs.value
+
+
+def default_segment(nsteps):
+    """Checkpoint spacing that minimises the stored states (checkpoints + one segment)."""
+    return max(1, int(round(float(nsteps) ** 0.5)))
+
+
 def lbm_wenoc_destroy(h):
     if h:
         load().lbm_wenoc_destroy(h)
@@ -311,6 +339,20 @@ class Simulation:
 
     def status(self):
         return lbm_wenoc_status(self.handle)
+
+    def deposit_gradient(self, c0, nsteps, segment=None):
+        """Run nsteps from c0 (fluid at rest) and return (J, dJ/dc0, dJ/dVs): J the
+        deposited mass, dJ/dc0 a device tensor of the grid's shape.  The handle must be
+        initialised again before further stepping."""
+        import torch
+        segment = default_segment(nsteps) if segment is None else int(segment)
+        c = self._as_input(c0, self.grid)
+        nbytes = lbm_wenoc_gradient_workspace_bytes(self.params, nsteps, segment)
+        adj = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        grad = torch.empty(self.grid, dtype=self.dtype, device="cuda")
+        self._keep = (c, None)
+        J, dvs = lbm_wenoc_deposit_gradient(self.handle, c, nsteps, segment, adj, nbytes, grad)
+        return J, grad, dvs
 
 
 # ---- batched simulations ---------------------------------------------------------------
