@@ -31,6 +31,8 @@ WORKLOADS = {
     "3d": (workloads.MAIN_3D, "coupled LBM+WENO5 GLUPS (3D D3Q19 256x256x512 FP32)", "D3Q19"),
 }
 WL, METRIC, LATTICE = WORKLOADS["2d"]
+ADJOINT_METRIC = ("gradient of the deposited mass wrt c0 and Vs, GLUPS of the reverse-mode pass "
+                  "(2D D2Q9 512x1024 FP32, 2000 steps, checkpoint every 100)")
 BATCH_METRIC = "coupled LBM+WENO5 GLUPS, batched sweep of 64 D2Q9 FP32 instances (256x512..1024x2048)"
 UNIT = "GLUPS"
 
@@ -407,6 +409,86 @@ def bench_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_adjoint(args):
+    """Reverse-mode gradient of the deposited mass on the 512 x 1024 lattice (2000 steps,
+    state kept every 100): time of one lbm_wenoc_deposit_gradient call (forward with
+    checkpoints, per-segment recompute, reverse sweep) against the plain forward of the
+    same steps.  GLUPS = nodes x steps / gradient time.  e2e: the torch.autograd path
+    from a pinned host c0 to dJ/dc0 back in host memory."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2106_07694_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    from paper_2106_07694_gb300.autograd import deposited_mass
+    wl = workloads.ADJOINT_2D
+    # the gradient is defined over the whole 2000-step horizon; the overrides only serve
+    # small profiling captures
+    nsteps = args.adjoint_steps or wl.steps
+    seg = args.adjoint_segment or wl.extra["segment"]
+    kw = dict(phys_kwargs(wl), lf_alpha=wl.extra["lf_alpha"])
+    c0 = torch.from_numpy(wl.initial_c().astype(np.float32)).cuda()
+    sim = lw.Simulation(wl.shape, **kw)
+    nbytes = lw.lbm_wenoc_gradient_workspace_bytes(sim.params, nsteps, seg)
+    adj = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    grad = torch.empty(c0.shape, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):  # forward alone
+        sim.init(c0)
+        sim.step(nsteps)
+    torch.cuda.synchronize()
+    e0.record()
+    sim.init(c0)
+    sim.step(nsteps)
+    e1.record()
+    J_fwd = sim.deposit
+    fwd_ms = e0.elapsed_time(e1)
+    lw.lbm_wenoc_deposit_gradient(sim.handle, c0, nsteps, seg, adj, nbytes, grad)  # warm-up
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = lw.lbm_wenoc_launch_count(sim.handle)
+    e0.record()
+    J, dvs = lw.lbm_wenoc_deposit_gradient(sim.handle, c0, nsteps, seg, adj, nbytes, grad)
+    e1.record()
+    torch.cuda.synchronize()
+    grad_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = lw.lbm_wenoc_launch_count(sim.handle) - l0
+    if J != J_fwd:
+        raise RuntimeError("forward of the gradient call differs from the plain forward")
+    # e2e through autograd: pinned host c0 in, dJ/dc0 back to pinned host memory
+    host_c0 = c0.cpu().pin_memory()
+    host_g = torch.empty(c0.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x = host_c0.cuda(non_blocking=True).requires_grad_(True)
+    vs = torch.tensor(wl.settling_velocity, dtype=torch.float64, requires_grad=True)
+    kw2 = {k: v for k, v in kw.items() if k != "settling_velocity"}
+    out = deposited_mass(x, vs, nsteps, wl.shape, segment=seg, **kw2)
+    out.backward()
+    host_g.copy_(x.grad, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    nodes = wl.nodes
+    value = nodes * nsteps / (grad_ms * 1e-3) / 1e9
+    line = {
+        "metric": ADJOINT_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+        "warmup": args.warmup, "ms_per_step": grad_ms / nsteps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": nodes, "segment": seg, "lf_alpha": kw["lf_alpha"],
+                   "adjoint_workspace_bytes": nbytes, "l2": "working set > L2 (states of one segment)"},
+        "forward": {"ms": fwd_ms, "glups": nodes * nsteps / (fwd_ms * 1e-3) / 1e9},
+        "gradient_over_forward": grad_ms / fwd_ms,
+        "J": J, "dJ_dVs": dvs, "grad_l2": float(torch.linalg.vector_norm(grad.double())),
+        "e2e": {"value": nodes * nsteps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * nodes / nsteps,
+                "d2h_bytes_per_step": (4 * nodes + 8) / nsteps},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    sim.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,7 +497,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batch"],
+    ap.add_argument("--adjoint-steps", type=int, default=0, help="override the horizon (profiling only)")
+    ap.add_argument("--adjoint-segment", type=int, default=0, help="override the checkpoint spacing")
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batch", "adjoint"],
                     help="2d: the 2048x4096 D2Q9 case the metric is quoted on; 3d: 256x256x512 D3Q19")
     args = ap.parse_args()
     global WL, METRIC, LATTICE
@@ -425,6 +509,13 @@ def main():
                               "the oracle is timed on the single-instance workloads"}))
             return
         bench_batch(args)
+        return
+    if args.workload == "adjoint":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the gradient has no oracle arm; "
+                              "the oracle is timed on the single-instance workloads"}))
+            return
+        bench_adjoint(args)
         return
     WL, METRIC, LATTICE = WORKLOADS[args.workload]
     if args.warmup < 3:

@@ -1,17 +1,18 @@
 // Reverse-mode (adjoint) kernels of the 2D coupled step, for the gradient of the
 // deposited mass (Sec. 4, m_b) with respect to the initial concentration and to Vs.
 //
-// Forward step n (see lbm_kernels.cuh, transport_kernels.cuh):
+// Forward step n (lbm_kernels.cuh, transport kernels):
 //   u = U(g, c); g' = Stream(Collide(g, F(c)));
 //   c1 = c + L(c; u); c2 = 3/4 c + 1/4 c1 + 1/4 L(c1; u); c' = 1/3 c + 2/3 c2 + 2/3 L(c2; u);
 //   J += Vs sum_floor(c/6 + c1/6 + 2 c2/3).
-// Its adjoint, given lambda(c'), lambda(g') and the recomputed u, c1, c2, runs the three
-// transport stages backwards (adj_stage_kernel scatters the face-flux derivatives with
-// atomics: Jacobian-transpose of L with respect to its input and to u, including the
-// WENO5-JS nonlinear weights), then the fluid step backwards (adj_fluid_kernel: reverse
-// streaming with bounce-back, transpose of the BGK-Guo collision, the velocity chain
-// u = (j + F/2)/rho, and the buoyancy F_y = -A c).  Lax-Friedrichs alpha is a fixed
-// parameter here (the caller sets lf_alpha), so d/dVs holds alpha fixed.
+// Given lambda(c') and lambda(g') and the stored u, c1, c2 of the step, one reverse step
+// is four launches: the three transport stages backwards (adj_stage_kernel<3,2,1>:
+// Jacobian-transpose of L with respect to its input and to u, WENO5-JS nonlinear weights
+// included, scattered with atomics), then the fluid step backwards (adj_fluid_kernel:
+// reverse streaming with bounce-back, transpose of the BGK-Guo collision, the velocity
+// chain u = (j + F/2)/rho, the buoyancy F_y = -A c), which also sets up the accumulators
+// of the next reverse step.  The Lax-Friedrichs alpha is a fixed parameter here (the
+// caller sets lf_alpha), so d/dVs holds alpha fixed.
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
@@ -19,13 +20,17 @@
 
 namespace lw {
 
+// Adjoint fields of one reverse step.  mu = lambda(c^{n+1}) (read by stage 3, then
+// overwritten with lambda(c^n) by the fluid kernel); lc2, lc1, lc accumulate lambda of
+// c2, c1 and c^n; lam_u = lambda(u) [2][n], zeroed again by the fluid kernel.
 template <typename T>
-struct AdjArgs {
-  const T* cs;    // stage input field (c, c1 or c2)
-  const T* lamL;  // adjoint of the stage rate L(cs)
-  T* lam_cs;      // adjoint of cs (accumulated)
-  T* lam_u;       // adjoint of u, [2][n] (accumulated)
-  double* lam_vs; // adjoint of Vs (accumulated)
+struct AdjFields {
+  T* mu;
+  T* lc2;
+  T* lc1;
+  T* lc;
+  T* lam_u;
+  double* lam_vs;
 };
 
 // WENO5-JS face value of the scaled values v[0..4] (upwind side first) and its partial
@@ -66,30 +71,44 @@ __device__ __forceinline__ T weno5_value_grad(const T (&v)[5], T (&dv)[5]) {
 __device__ __forceinline__ void atomic_add_t(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add_t(double* p, double v) { atomicAdd(p, v); }
 
-// Adjoint of one stage's rate L(cs; u): one thread per node handles the face on its +
-// side along x and along y (and the floor face below row 0).
-template <typename T>
-__global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjArgs<T> j) {
+// Adjoint of SSP-RK3 stage STAGE of the transport, one node per thread.
+//   STAGE 3: c' = 1/3 c + 2/3 (c2 + L(c2)):  lamL = 2/3 mu, scatter into lc2;
+//   STAGE 2: c2 = 3/4 c + 1/4 (c1 + L(c1)):  lamL = 1/4 lc2, scatter into lc1; direct
+//            terms lc1 += 1/4 lc2, lc += 3/4 lc2;
+//   STAGE 1: c1 = c + L(c):                  lamL = lc1, scatter into lc; lc += lc1.
+// The thread of node i handles the faces on its + side along x and along y: for each, the
+// adjoint of the face flux lamF = lamL[i+1] - lamL[i] times the flux derivatives with
+// respect to the six stencil values of c and of the velocity, added with atomics (the
+// node's own entry merged into one add).  The floor face below row 0 (F = -Vs c) and the
+// deposit's RK3 b-weights (c/6 + c1/6 + 2 c2/3 on the floor, times Vs) give the Vs adjoint.
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjFields<T> f) {
   __shared__ double sh[4];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   const int nx = a.nx, ny = a.ny;
+  const T* __restrict__ cs = STAGE == 3 ? a.c2 : (STAGE == 2 ? a.c1 : a.c);
+  const T* lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
+  const T lscale = STAGE == 3 ? T(2.0 / 3.0) : (STAGE == 2 ? T(0.25) : T(1));
+  T* lam_cs = STAGE == 3 ? f.lc2 : (STAGE == 2 ? f.lc1 : f.lc);
   double vs_acc = 0.0;
   if (x < nx) {
     const long long n = a.n;
     const long long node = (long long)y * nx + x;
     const T alpha = a.alpha, ia = a.inv_alpha;
+    const T lam_here = lscale * lsrc[node];
+    T own = T(0);  // everything this thread adds to lam_cs[node]
+    if (STAGE == 2) {
+      own = lam_here;                 // 1/4 lc2: c1 enters c2 directly
+      f.lc[node] += T(3) * lam_here;  // 3/4 lc2: c^n enters c2 (no other writer of lc here)
+    } else if (STAGE == 1) {
+      own = lam_here;                 // lc1: c^n enters c1 directly
+    }
     for (int d = 0; d < 2; ++d) {
       const bool vert = d == 1;
       if (vert && y == ny - 1) continue;  // lid: no flux
-      // adjoint of the face flux F_{+1/2}: L_node -= F, L_next += F
-      long long next;
-      if (!vert)
-        next = (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
-      else
-        next = node + nx;
-      const T lamF = j.lamL[next] - j.lamL[node];
-      // stencil k = -2..3 along d: node index, ghost flag
+      const long long next = vert ? node + nx : (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
+      const T lamF = lscale * lsrc[next] - lam_here;  // F_{+1/2} leaves node, enters next
       long long idx[6];
       bool ghost[6];
       T cv[6], wv[6];
@@ -111,7 +130,7 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjArgs<T> j)
           idx[k + 2] = (long long)y * nx + p;
         }
         ghost[k + 2] = g;
-        cv[k + 2] = j.cs[idx[k + 2]];
+        cv[k + 2] = cs[idx[k + 2]];
         T ud = a.u[(long long)d * n + idx[k + 2]];
         if (g) ud = -ud;
         wv[k + 2] = (ud - (vert ? a.vs : T(0))) * ia;  // w / alpha
@@ -119,13 +138,13 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjArgs<T> j)
       T hp[5], hm[5], gp[5], gm[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        hp[k] = T(0.5) * (wv[k] + T(1)) * cv[k];       // h+ at stencil k-2 (k = 0..4)
+        hp[k] = T(0.5) * (wv[k] + T(1)) * cv[k];          // h+ at stencil k-2
         hm[k] = T(0.5) * (wv[5 - k] - T(1)) * cv[5 - k];  // h- mirrored: stencil 3..-1
       }
       weno5_value_grad<T>(hp, gp);
       weno5_value_grad<T>(hm, gm);
       // F = alpha (v+ + v-) + kappa (c_0 - c_1): dF/dh = alpha dv; dh/dc = (w/alpha +- 1)/2,
-      // dh/dw_phys = c / (2 alpha) -> dF/dw_phys = dv c / 2
+      // dF/dw_phys = dv c / 2
       T dFdc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
       T dFdw[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -139,17 +158,21 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjArgs<T> j)
       dFdc[3] -= a.kappa;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        atomic_add_t(j.lam_cs + idx[k], lamF * dFdc[k]);
+        if (k == 2)  // the node itself (never a ghost: y is inside the lattice)
+          own += lamF * dFdc[k];
+        else
+          atomic_add_t(lam_cs + idx[k], lamF * dFdc[k]);
         const T du = ghost[k] ? -dFdw[k] : dFdw[k];  // w = +-u - Vs (vertical) or u (horizontal)
-        atomic_add_t(j.lam_u + (long long)d * n + idx[k], lamF * du);
+        atomic_add_t(f.lam_u + (long long)d * n + idx[k], lamF * du);
         if (vert) vs_acc -= (double)(lamF * dFdw[k]);
       }
     }
-    if (y == 0) {  // floor face below row 0: F = -Vs c_0, enters L_0 with +
-      const T lam = j.lamL[node];
-      atomic_add_t(j.lam_cs + node, -a.vs * lam);
-      vs_acc -= (double)(j.cs[node] * lam);
+    if (y == 0) {
+      own -= a.vs * lam_here;  // floor face below row 0: F = -Vs c_0 enters L_0 with +
+      vs_acc -= (double)(cs[node] * lam_here);
+      vs_acc += (double)cs[node] * (STAGE == 3 ? 2.0 / 3.0 : 1.0 / 6.0);  // deposit b-weights
     }
+    atomic_add_t(lam_cs + node, own);
   }
   // block sum of the Vs adjoint, one double atomic per block
 #pragma unroll
@@ -159,47 +182,40 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjArgs<T> j)
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    if (s != 0.0) atomicAdd(j.lam_vs, s);
+    if (s != 0.0) atomicAdd(f.lam_vs, s);
   }
 }
 
-// Elementwise combinations of the adjoint fields (n nodes):
-// out = ca * A + cb * B (+ floor term: fl on the first nfloor nodes)
+// Seed the accumulators of a reverse step at node k from m = lambda(c') there: the
+// direct terms 2/3 m (into lc2) and 1/3 m (into lc), and the floor terms of the deposit.
 template <typename T>
-__global__ void adj_axpby_kernel(T* out, const T* A, T ca, const T* B, T cb, long long n, long long nfloor, T fl) {
+__device__ __forceinline__ void adj_seed(const AdjFields<T>& f, long long k, bool floor, T m, T vs) {
+  f.lc2[k] = T(2.0 / 3.0) * m + (floor ? T(2.0 / 3.0) * vs : T(0));
+  f.lc1[k] = floor ? vs / T(6) : T(0);
+  f.lc[k] = T(1.0 / 3.0) * m + (floor ? vs / T(6) : T(0));
+}
+
+// State before the last reverse step: J does not depend on c^N or the final populations,
+// so mu = 0 and lambda(u) = 0.
+template <typename T>
+__global__ void adj_init_kernel(AdjFields<T> f, long long n, int nx, T vs) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  T v = ca * A[k];
-  if (B) v += cb * B[k];
-  if (k < nfloor) v += fl;
-  out[k] = v;
-}
-
-// Deposit's direct dependence on Vs: lam_vs += sum_floor(c/6 + c1/6 + 2 c2/3)
-template <typename T>
-__global__ void adj_deposit_vs_kernel(const T* c, const T* c1, const T* c2, long long nfloor, double* lam_vs) {
-  __shared__ double sh[8];
-  double acc = 0.0;
-  for (long long k = threadIdx.x; k < nfloor; k += blockDim.x)
-    acc += ((double)c[k] + (double)c1[k]) / 6.0 + (double)c2[k] * (2.0 / 3.0);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    *lam_vs += s;
-  }
+  f.mu[k] = T(0);
+  adj_seed<T>(f, k, k < nx, T(0), vs);
+  f.lam_u[k] = T(0);
+  f.lam_u[n + k] = T(0);
+  if (k == 0) *f.lam_vs = 0.0;
 }
 
 // Adjoint of the fluid step at each node.  Inputs: the populations of step n (AA layout
 // with its parity), c^n, lambda of the streamed populations of step n+1 (natural layout
-// lam_next[i][node]), lambda(u) from the transport.  Outputs: lambda of the populations
-// of step n (natural layout), and -A lambda(F_y) added to lambda(c^n).
+// lam_next[i][node]), lambda(u) and the transport part of lambda(c^n) in lc.  Outputs:
+// lambda of the populations of step n (natural layout) and lambda(c^n) = lc - A
+// lambda(F_y) in mu; then seeds lc2, lc1, lc for the step before and zeroes lambda(u).
 template <typename T, int PARITY>
-__global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, const T* lam_next, const T* lam_u, T* lam_out,
-                                                        T* lam_c) {
+__global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, AdjFields<T> f, const T* lam_next,
+                                                        T* lam_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= a.nx) return;
@@ -229,7 +245,7 @@ __global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, const T* lam_
       mu[i] = lam_next[D2Q9::opp(i) * n + node];
   }
   // collision g* = (1 - w) g + w geq(drho, u) + src(u, F)
-  T lam_drho = T(0), lux = lam_u[node], luy = lam_u[n + node], lFx = T(0), lFy = T(0);
+  T lam_drho = T(0), lux = f.lam_u[node], luy = f.lam_u[n + node], lFy = T(0);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const T wi = T(D2Q9::w(i));
@@ -241,20 +257,21 @@ __global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, const T* lam_
     const T kq = lgeq * wi * rho, ks = lsrc * a.guo * wi;
     lux += kq * (T(3) * cx + T(9) * cu * cx - T(3) * ux) + ks * (T(-3) * Fx + T(9) * cx * cF);
     luy += kq * (T(3) * cy + T(9) * cu * cy - T(3) * uy) + ks * (T(-3) * Fy + T(9) * cy * cF);
-    lFx += ks * (T(3) * cx - T(3) * ux + T(9) * cu * cx);
     lFy += ks * (T(3) * cy - T(3) * uy + T(9) * cu * cy);
   }
   // u = (j + F/2)/rho
   const T ljx = lux / rho, ljy = luy / rho;
-  lFx += lux / (T(2) * rho);
   lFy += luy / (T(2) * rho);
   lam_drho -= (lux * ux + luy * uy) / rho;
   const T keep = T(1) - a.omega;
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     lam_out[i * n + node] = keep * mu[i] + lam_drho + ljx * T(D2Q9::cx(i)) + ljy * T(D2Q9::cy(i));
-  lam_c[node] += -a.A * lFy;
-  (void)lFx;
+  const T lam_c = f.lc[node] - a.A * lFy;
+  f.mu[node] = lam_c;
+  adj_seed<T>(f, node, y == 0, lam_c, a.vs);
+  f.lam_u[node] = T(0);
+  f.lam_u[n + node] = T(0);
 }
 
 }  // namespace lw

@@ -930,6 +930,11 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
 
 // ------------------------------------------------------------------------------------
 // Gradient of the deposited mass by checkpoint-and-recompute and the adjoint kernels.
+//
+// Adjoint workspace: a checkpoint (populations + c, the handle's layout from g to c) at
+// the start of every segment; one segment of step records (the handle's layout from g to
+// u: populations and c before the step, c1, c2 and u of the step); lambda of the
+// populations (two buffers, natural layout); mu, lc2, lc1, lc, lambda(u); lambda(Vs).
 
 namespace {
 
@@ -938,99 +943,66 @@ bool gradient_params_ok(const lbm_wenoc* h) {
 }
 
 struct GradLayout {
-  size_t ckpt, seg, lg0, lg1, mu, lc2, lc1, lc, S, lu, vs, total, state;
+  size_t ckpt, rec, lg0, lg1, mu, lc2, lc1, lc, lu, vs, total;
+  size_t ckpt_bytes, rec_bytes;  // one checkpoint, one step record
   int64_t nseg;
 };
 
 GradLayout grad_layout(const lbm_wenoc_params& p, int64_t nsteps, int32_t segment) {
+  const Layout L = make_layout(p);
   const size_t n = (size_t)p.nx * p.ny;
   const size_t es = (p.flags & LW_FP64) ? 8 : 4;
   GradLayout G{};
   G.nseg = (nsteps + segment - 1) / segment;
-  G.state = align_up((9 + 1) * n * es, 256);
+  G.ckpt_bytes = align_up(L.c + n * es - L.g, 256);
+  G.rec_bytes = align_up(L.u + 2 * n * es - L.g, 256);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off = align_up(off + bytes, 256);
     return o;
   };
-  G.ckpt = take(G.state * (size_t)std::max<int64_t>(G.nseg, 1));
-  G.seg = take(G.state * (size_t)segment);
+  G.ckpt = take(G.ckpt_bytes * (size_t)G.nseg);
+  G.rec = take(G.rec_bytes * (size_t)segment);
   G.lg0 = take(9 * n * es);
   G.lg1 = take(9 * n * es);
   G.mu = take(n * es);
   G.lc2 = take(n * es);
   G.lc1 = take(n * es);
   G.lc = take(n * es);
-  G.S = take(n * es);
   G.lu = take(2 * n * es);
   G.vs = take(sizeof(double) * 4);
   G.total = off;
   return G;
 }
 
-// copy the handle's populations and c into / out of a state slot
-int save_state(lbm_wenoc* h, unsigned char* slot) {
-  const size_t es = h->fp64 ? 8 : 4, n = (size_t)h->n;
-  if (cudaMemcpyAsync(slot, h->ws + h->L.g, 9 * n * es, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
-    return LW_ECUDA;
-  if (cudaMemcpyAsync(slot + 9 * n * es, h->ws + h->L.c, n * es, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
-    return LW_ECUDA;
-  return LW_OK;
-}
-int load_state(lbm_wenoc* h, const unsigned char* slot) {
-  const size_t es = h->fp64 ? 8 : 4, n = (size_t)h->n;
-  if (cudaMemcpyAsync(h->ws + h->L.g, slot, 9 * n * es, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
-    return LW_ECUDA;
-  if (cudaMemcpyAsync(h->ws + h->L.c, slot + 9 * n * es, n * es, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
-    return LW_ECUDA;
-  return LW_OK;
+int copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
-// One reverse step: the handle holds the state of step n (populations with parity par,
-// c); mu = lambda(c^{n+1}) in, lam_c = lambda(c^n) out; lam_next / lam_out = lambda of
-// the populations of steps n+1 / n (natural layout).
+// Reverse step over the step record `rec` (populations with parity par): mu = lambda(c^{n+1})
+// in, lambda(c^n) out; lam_next / lam_out = lambda of the populations of steps n+1 / n.
 template <typename T>
-int adjoint_step(lbm_wenoc* h, int par, const GradLayout& G, unsigned char* aw, T* mu, T* lc, T* lam_next,
+int adjoint_step(lbm_wenoc* h, int par, const unsigned char* rec, const lw::AdjFields<T>& f, const T* lam_next,
                  T* lam_out) {
   Args<T> a = make_args<T>(h);
+  const Layout& L = h->L;
+  unsigned char* r = const_cast<unsigned char*>(rec);
+  a.g = reinterpret_cast<T*>(r);
+  a.c = reinterpret_cast<T*>(r + (L.c - L.g));
+  a.c1 = reinterpret_cast<T*>(r + (L.c1 - L.g));
+  a.c2 = reinterpret_cast<T*>(r + (L.c2 - L.g));
+  a.u = reinterpret_cast<T*>(r + (L.u - L.g));
   cudaStream_t s = h->stream;
-  const long long n = h->n, nfloor = a.nx;
   const dim3 blk(kLbmThreads), grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, 1);
-  const int eb = 256, eg = (int)((n + eb - 1) / eb);
-  T* lc2 = reinterpret_cast<T*>(aw + G.lc2);
-  T* lc1 = reinterpret_cast<T*>(aw + G.lc1);
-  T* S = reinterpret_cast<T*>(aw + G.S);
-  T* lu = reinterpret_cast<T*>(aw + G.lu);
-  double* lvs = reinterpret_cast<double*>(aw + G.vs);
-  const T vs = a.vs;
-  // recompute u^n, c1, c2
+  lw::adj_stage_kernel<T, 3><<<grd, blk, 0, s>>>(a, f);
+  lw::adj_stage_kernel<T, 2><<<grd, blk, 0, s>>>(a, f);
+  lw::adj_stage_kernel<T, 1><<<grd, blk, 0, s>>>(a, f);
   if (par == 0)
-    lw::fields_kernel<D2Q9, T, 0><<<grd, blk, 0, s>>>(a, nullptr, a.u);
+    lw::adj_fluid_kernel<T, 0><<<grd, blk, 0, s>>>(a, f, lam_next, lam_out);
   else
-    lw::fields_kernel<D2Q9, T, 1><<<grd, blk, 0, s>>>(a, nullptr, a.u);
-  lw::rk_stage_kernel<T, 2, 1><<<grd, blk, 0, s>>>(a);
-  lw::rk_stage_kernel<T, 2, 2><<<grd, blk, 0, s>>>(a);
-  if (cudaMemsetAsync(lu, 0, 2 * n * sizeof(T), s) != cudaSuccess) return LW_ECUDA;
-  // deposit: dJ/dVs direct term
-  lw::adj_deposit_vs_kernel<T><<<1, 256, 0, s>>>(a.c, a.c1, a.c2, nfloor, lvs);
-  // stage 3: c' = 1/3 c + 2/3 c2 + 2/3 L(c2)
-  lw::adj_axpby_kernel<T><<<eg, eb, 0, s>>>(lc2, mu, T(2.0 / 3.0), nullptr, T(0), n, nfloor, T(2.0 / 3.0) * vs);
-  lw::adj_axpby_kernel<T><<<eg, eb, 0, s>>>(S, mu, T(2.0 / 3.0), nullptr, T(0), n, 0, T(0));
-  lw::adj_stage_kernel<T><<<grd, blk, 0, s>>>(a, lw::AdjArgs<T>{a.c2, S, lc2, lu, lvs});
-  // stage 2: c2 = 3/4 c + 1/4 c1 + 1/4 L(c1)
-  lw::adj_axpby_kernel<T><<<eg, eb, 0, s>>>(lc1, lc2, T(0.25), nullptr, T(0), n, nfloor, vs / T(6));
-  lw::adj_axpby_kernel<T><<<eg, eb, 0, s>>>(S, lc2, T(0.25), nullptr, T(0), n, 0, T(0));
-  lw::adj_stage_kernel<T><<<grd, blk, 0, s>>>(a, lw::AdjArgs<T>{a.c1, S, lc1, lu, lvs});
-  // stage 1: c1 = c + L(c); lambda(c) = 1/3 mu + 3/4 lc2 + lc1 + Vs/6 (floor) + L^T lc1
-  lw::adj_axpby_kernel<T><<<eg, eb, 0, s>>>(lc, mu, T(1.0 / 3.0), lc2, T(0.75), n, nfloor, vs / T(6));
-  lw::adj_axpby_kernel<T><<<eg, eb, 0, s>>>(lc, lc, T(1), lc1, T(1), n, 0, T(0));
-  lw::adj_stage_kernel<T><<<grd, blk, 0, s>>>(a, lw::AdjArgs<T>{a.c, lc1, lc, lu, lvs});
-  // fluid step
-  if (par == 0)
-    lw::adj_fluid_kernel<T, 0><<<grd, blk, 0, s>>>(a, lam_next, lu, lam_out, lc);
-  else
-    lw::adj_fluid_kernel<T, 1><<<grd, blk, 0, s>>>(a, lam_next, lu, lam_out, lc);
+    lw::adj_fluid_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, lam_next, lam_out);
+  h->launches += 4;
   return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
@@ -1039,48 +1011,57 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
                           const GradLayout& G, void* grad_c0, double* dJ_dVs, double* J) {
   int rc = lbm_wenoc_init(h, c0, nullptr);
   if (rc != LW_OK) return rc;
+  cudaStream_t s = h->stream;
+  const Layout& L = h->L;
+  unsigned char* state = h->ws + L.g;
+  // forward, keeping the state at the start of every segment
   std::vector<int> ck_parity((size_t)G.nseg);
-  for (int64_t t = 0; t < nsteps; ++t) {
-    if (t % segment == 0) {
-      ck_parity[(size_t)(t / segment)] = h->parity;
-      if ((rc = save_state(h, aw + G.ckpt + (size_t)(t / segment) * G.state)) != LW_OK) return rc;
-    }
-    if ((rc = lbm_wenoc_step(h, 1)) != LW_OK) return rc;
+  for (int64_t sg = 0; sg < G.nseg; ++sg) {
+    const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
+    ck_parity[(size_t)sg] = h->parity;
+    if ((rc = copy_d2d(aw + G.ckpt + (size_t)sg * G.ckpt_bytes, state, G.ckpt_bytes, s)) != LW_OK) return rc;
+    if ((rc = lbm_wenoc_step(h, len)) != LW_OK) return rc;
   }
   if ((rc = lbm_wenoc_deposited_mass(h, J)) != LW_OK) return rc;
   const size_t n = (size_t)h->n;
+  lw::AdjFields<T> f;
+  f.mu = reinterpret_cast<T*>(aw + G.mu);
+  f.lc2 = reinterpret_cast<T*>(aw + G.lc2);
+  f.lc1 = reinterpret_cast<T*>(aw + G.lc1);
+  f.lc = reinterpret_cast<T*>(aw + G.lc);
+  f.lam_u = reinterpret_cast<T*>(aw + G.lu);
+  f.lam_vs = reinterpret_cast<double*>(aw + G.vs);
   T* lg[2] = {reinterpret_cast<T*>(aw + G.lg0), reinterpret_cast<T*>(aw + G.lg1)};
-  T* mu = reinterpret_cast<T*>(aw + G.mu);
-  T* lc = reinterpret_cast<T*>(aw + G.lc);
-  if (cudaMemsetAsync(lg[0], 0, 9 * n * sizeof(T), h->stream) != cudaSuccess) return LW_ECUDA;
-  if (cudaMemsetAsync(mu, 0, n * sizeof(T), h->stream) != cudaSuccess) return LW_ECUDA;
-  if (cudaMemsetAsync(aw + G.vs, 0, sizeof(double), h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemsetAsync(lg[0], 0, 9 * n * sizeof(T), s) != cudaSuccess) return LW_ECUDA;
+  lw::adj_init_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, (long long)n, h->p.nx, (T)h->p.settling_velocity);
+  h->launches += 1;
   int cur = 0;
-  std::vector<int> seg_parity((size_t)segment);
+  std::vector<int> rec_parity((size_t)segment);
   for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
-    const int64_t s0 = sg * segment, len = std::min<int64_t>(segment, nsteps - s0);
-    if ((rc = load_state(h, aw + G.ckpt + (size_t)sg * G.state)) != LW_OK) return rc;
+    const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
+    // recompute the segment from its checkpoint, recording every step
+    if ((rc = copy_d2d(state, aw + G.ckpt + (size_t)sg * G.ckpt_bytes, G.ckpt_bytes, s)) != LW_OK) return rc;
     h->parity = ck_parity[(size_t)sg];
     h->cur = 0;
-    for (int64_t k = 0; k < len; ++k) {  // recompute the segment, keeping every state
-      seg_parity[(size_t)k] = h->parity;
-      if ((rc = save_state(h, aw + G.seg + (size_t)k * G.state)) != LW_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) {
+      unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
+      rec_parity[(size_t)k] = h->parity;
+      if ((rc = copy_d2d(rec, state, G.ckpt_bytes, s)) != LW_OK) return rc;  // populations, c^n
       if ((rc = lbm_wenoc_step(h, 1)) != LW_OK) return rc;
+      if ((rc = copy_d2d(rec + (L.c1 - L.g), h->ws + L.c1, L.u + 2 * n * sizeof(T) - L.c1, s)) != LW_OK)
+        return rc;  // c1, c2, u of the step
     }
     for (int64_t k = len - 1; k >= 0; --k) {
-      if ((rc = load_state(h, aw + G.seg + (size_t)k * G.state)) != LW_OK) return rc;
-      h->parity = seg_parity[(size_t)k];
-      if ((rc = adjoint_step<T>(h, h->parity, G, aw, mu, lc, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
-      std::swap(mu, lc);  // lambda(c^n) becomes the input of step n-1
+      const unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
+      if ((rc = adjoint_step<T>(h, rec_parity[(size_t)k], rec, f, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
       cur ^= 1;
     }
   }
   // mu now holds lambda(c^0)
   cudaMemcpyKind k = is_device_pointer(grad_c0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (cudaMemcpyAsync(grad_c0, mu, n * sizeof(T), k, h->stream) != cudaSuccess) return LW_ECUDA;
-  if (cudaMemcpyAsync(dJ_dVs, aw + G.vs, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
-    return LW_ECUDA;
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemcpyAsync(grad_c0, f.mu, n * sizeof(T), k, s) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemcpyAsync(dJ_dVs, f.lam_vs, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LW_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LW_ECUDA;
   h->initialised = false;  // the handle holds a recomputed intermediate state
   return sync_and_status(h);
 }

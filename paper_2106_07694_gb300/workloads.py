@@ -83,6 +83,11 @@ MAIN_2D = Workload("d2q9_2048x4096_f32", (2048, 4096), "f32", 20000)
 # 3D D3Q19, 256 x 256 x 512, FP32.
 MAIN_3D = Workload("d3q19_256x256x512_f32", (256, 256, 512), "f32", 10000, gravity=2e-5)
 
+# Gradient of the deposited mass: 2D D2Q9, 512 x 1024, FP32, 2000 steps, state kept
+# every 100 steps; Lax-Friedrichs alpha fixed at Vs + 0.1 (the default u_cap).
+ADJOINT_2D = Workload("d2q9_512x1024_f32_adjoint", (512, 1024), "f32", 2000,
+                      extra=dict(segment=100, lf_alpha=1e-3 + 0.1))
+
 # Sweep grid of the 2048 x 4096 case: buoyancy amplitude x settling velocity.
 MAIN_2D_SWEEP = [(a, vs) for a in (1e-5, 2e-5, 5e-5) for vs in (5e-4, 1e-3, 2e-3)]
 
