@@ -460,15 +460,19 @@ def bench_adjoint(args):
     # e2e through autograd: pinned host c0 in, dJ/dc0 back to pinned host memory
     host_c0 = c0.cpu().pin_memory()
     host_g = torch.empty(c0.shape, dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    x = host_c0.cuda(non_blocking=True).requires_grad_(True)
-    vs = torch.tensor(wl.settling_velocity, dtype=torch.float64, requires_grad=True)
     kw2 = {k: v for k, v in kw.items() if k != "settling_velocity"}
-    out = deposited_mass(x, vs, nsteps, wl.shape, segment=seg, **kw2)
-    out.backward()
-    host_g.copy_(x.grad, non_blocking=True)
-    torch.cuda.synchronize()
+
+    def e2e_call():
+        x = host_c0.cuda(non_blocking=True).requires_grad_(True)
+        vs = torch.tensor(wl.settling_velocity, dtype=torch.float64, requires_grad=True)
+        out = deposited_mass(x, vs, nsteps, wl.shape, segment=seg, **kw2)
+        out.backward()
+        host_g.copy_(x.grad, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_call()  # warm-up: the wrapper allocates its handle and workspace once
+    t0 = time.perf_counter()
+    e2e_call()
     e2e_s = time.perf_counter() - t0
     nodes = wl.nodes
     value = nodes * nsteps / (grad_ms * 1e-3) / 1e9

@@ -182,7 +182,8 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b);
  * Requires a 2D handle with walls, not frozen, without LW_FUSED_RK3, and an explicit
  * lf_alpha > 0 (LW_EINVAL otherwise).  adj_workspace: caller-owned device memory of at
  * least lbm_wenoc_gradient_workspace_bytes() (checkpoints + one segment of states +
- * adjoint fields), 256-byte aligned.  Synchronises.  Afterwards the handle holds an
+ * adjoint fields, one stage's face records), 256-byte aligned.  Deterministic (no
+ * atomics): the same inputs give the same bits for any segment.  Synchronises.  Afterwards the handle holds an
  * intermediate state and must be initialised again before stepping. */
 int lbm_wenoc_gradient_workspace_bytes(const lbm_wenoc_params* p, int64_t nsteps, int32_t segment, size_t* bytes);
 int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t segment, void* adj_workspace,

@@ -8,10 +8,38 @@ gradient is needed the forward pass already runs the checkpointed forward + reve
 sweep of the library (one call), keeps dJ/dc0 and dJ/dVs, and the backward pass only
 scales them by the incoming gradient.  The Lax-Friedrichs alpha must be given
 (``lf_alpha``) and stays fixed under a change of Vs.
+
+The handle and its adjoint workspace of the last configuration are kept for the next
+call with the same configuration (an optimisation loop calls with the same sizes);
+``release()`` frees them.
 """
 import torch
 
 from . import lbm_wenoc as lw
+
+
+_cache = {}
+
+
+def release():
+    """Free the cached handle and workspace."""
+    for sim, _ in _cache.values():
+        sim.close()
+    _cache.clear()
+
+
+def _simulation(shape, vs, nsteps, segment, kw):
+    key = (tuple(shape), float(vs), int(nsteps), segment, tuple(sorted(kw.items())))
+    hit = _cache.get(key)
+    if hit is None:
+        release()
+        sim = lw.Simulation(shape, settling_velocity=float(vs), **kw)
+        seg = lw.default_segment(nsteps) if segment is None else int(segment)
+        nbytes = lw.lbm_wenoc_gradient_workspace_bytes(sim.params, nsteps, seg)
+        adj = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        grad = torch.empty(sim.grid, dtype=sim.dtype, device="cuda")
+        hit = _cache[key] = (sim, (seg, adj, nbytes, grad))
+    return hit
 
 
 class _DepositedMass(torch.autograd.Function):
@@ -19,18 +47,16 @@ class _DepositedMass(torch.autograd.Function):
     def forward(ctx, c0, vs, cfg):
         shape, nsteps, segment, kw = cfg
         need = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
-        sim = lw.Simulation(shape, settling_velocity=float(vs), **kw)
-        try:
-            if need:
-                J, g, dvs = sim.deposit_gradient(c0.detach(), nsteps, segment)
-                ctx.save_for_backward(g.to(c0.dtype).reshape(c0.shape),
-                                      torch.tensor(dvs, dtype=torch.float64, device=c0.device))
-            else:
-                sim.init(c0.detach())
-                sim.step(nsteps)
-                J = sim.deposit
-        finally:
-            sim.close()
+        sim, (seg, adj, nbytes, grad) = _simulation(shape, vs, nsteps, segment, kw)
+        c = c0.detach().to(sim.dtype).contiguous()
+        if need:
+            J, dvs = lw.lbm_wenoc_deposit_gradient(sim.handle, c, nsteps, seg, adj, nbytes, grad)
+            ctx.save_for_backward(grad.to(c0.dtype).reshape(c0.shape).clone(),
+                                  torch.tensor(dvs, dtype=torch.float64, device=c0.device))
+        else:
+            lw.lbm_wenoc_init(sim.handle, c)
+            lw.lbm_wenoc_step(sim.handle, nsteps)
+            J = lw.lbm_wenoc_deposited_mass(sim.handle)
         return torch.tensor(J, dtype=torch.float64, device=c0.device)
 
     @staticmethod

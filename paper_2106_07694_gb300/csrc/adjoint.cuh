@@ -6,13 +6,14 @@
 //   c1 = c + L(c; u); c2 = 3/4 c + 1/4 c1 + 1/4 L(c1; u); c' = 1/3 c + 2/3 c2 + 2/3 L(c2; u);
 //   J += Vs sum_floor(c/6 + c1/6 + 2 c2/3).
 // Given lambda(c') and lambda(g') and the stored u, c1, c2 of the step, one reverse step
-// is four launches: the three transport stages backwards (adj_stage_kernel<3,2,1>:
-// Jacobian-transpose of L with respect to its input and to u, WENO5-JS nonlinear weights
-// included, scattered with atomics), then the fluid step backwards (adj_fluid_kernel:
-// reverse streaming with bounce-back, transpose of the BGK-Guo collision, the velocity
-// chain u = (j + F/2)/rho, the buoyancy F_y = -A c), which also sets up the accumulators
-// of the next reverse step.  The Lax-Friedrichs alpha is a fixed parameter here (the
-// caller sets lf_alpha), so d/dVs holds alpha fixed.
+// is seven launches: the three transport stages backwards (for each, adj_faces_kernel
+// records every face's flux derivatives once and adj_gather_kernel sums, per node, the
+// records of the faces whose stencils contain it: the Jacobian-transpose of L with respect
+// to its input and to u, WENO5-JS nonlinear weights included), then the fluid step backwards (adj_fluid_kernel: reverse
+// streaming with bounce-back, transpose of the BGK-Guo collision, the velocity chain
+// u = (j + F/2)/rho, the buoyancy F_y = -A c).  The Lax-Friedrichs alpha is a fixed
+// parameter here (the caller sets lf_alpha), so d/dVs holds alpha fixed.  No atomics: results are
+// bitwise reproducible and independent of the checkpoint spacing.
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
@@ -22,7 +23,8 @@ namespace lw {
 
 // Adjoint fields of one reverse step.  mu = lambda(c^{n+1}) (read by stage 3, then
 // overwritten with lambda(c^n) by the fluid kernel); lc2, lc1, lc accumulate lambda of
-// c2, c1 and c^n; lam_u = lambda(u) [2][n], zeroed again by the fluid kernel.
+// c2, c1 and c^n (each written whole by its stage kernel); lam_u = lambda(u) [2][n]
+// (written by stage 3, accumulated by stages 2 and 1).
 template <typename T>
 struct AdjFields {
   T* mu;
@@ -30,7 +32,8 @@ struct AdjFields {
   T* lc1;
   T* lc;
   T* lam_u;
-  double* lam_vs;
+  double* lam_vs;   // dJ/dVs (written once at the end)
+  double* vs_part;  // per-CTA partial sums of dJ/dVs, accumulated over stages and steps
 };
 
 // WENO5-JS face value of the scaled values v[0..4] (upwind side first) and its partial
@@ -38,23 +41,24 @@ struct AdjFields {
 template <typename T>
 __device__ __forceinline__ T weno5_value_grad(const T (&v)[5], T (&dv)[5]) {
   const T a = v[0], b = v[1], c = v[2], d = v[3], e = v[4];
-  const T eps = T(1e-6);
-  const T q0 = (T(2) * a - T(7) * b + T(11) * c) / T(6);
-  const T q1 = (-b + T(5) * c + T(2) * d) / T(6);
-  const T q2 = (T(2) * c + T(5) * d - e) / T(6);
+  const T eps = T(1e-6), sixth = T(1.0 / 6.0);
+  const T q0 = (T(2) * a - T(7) * b + T(11) * c) * sixth;
+  const T q1 = (-b + T(5) * c + T(2) * d) * sixth;
+  const T q2 = (T(2) * c + T(5) * d - e) * sixth;
   const T s0 = a - T(2) * b + c, s1 = b - T(2) * c + d, s2 = c - T(2) * d + e;
   const T t0 = a - T(4) * b + T(3) * c, t1 = b - d, t2 = T(3) * c - T(4) * d + e;
-  const T A0 = eps + T(13.0 / 12.0) * s0 * s0 + T(0.25) * t0 * t0;
-  const T A1 = eps + T(13.0 / 12.0) * s1 * s1 + T(0.25) * t1 * t1;
-  const T A2 = eps + T(13.0 / 12.0) * s2 * s2 + T(0.25) * t2 * t2;
-  const T a0 = T(0.1) / (A0 * A0), a1 = T(0.6) / (A1 * A1), a2 = T(0.3) / (A2 * A2);
+  // reciprocals of eps + beta_m: four divisions in all
+  const T i0 = T(1) / (eps + T(13.0 / 12.0) * s0 * s0 + T(0.25) * t0 * t0);
+  const T i1 = T(1) / (eps + T(13.0 / 12.0) * s1 * s1 + T(0.25) * t1 * t1);
+  const T i2 = T(1) / (eps + T(13.0 / 12.0) * s2 * s2 + T(0.25) * t2 * t2);
+  const T a0 = T(0.1) * i0 * i0, a1 = T(0.6) * i1 * i1, a2 = T(0.3) * i2 * i2;
   const T inv = T(1) / (a0 + a1 + a2);
   const T w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
   const T val = w0 * q0 + w1 * q1 + w2 * q2;
-  // weight-sensitivity factors r_m = (q_m - val) w_m (-2 / A_m)
-  const T r0 = (q0 - val) * w0 * (T(-2) / A0);
-  const T r1 = (q1 - val) * w1 * (T(-2) / A1);
-  const T r2 = (q2 - val) * w2 * (T(-2) / A2);
+  // weight-sensitivity factors r_m = (q_m - val) w_m (-2 / (eps + beta_m))
+  const T r0 = T(-2) * (q0 - val) * w0 * i0;
+  const T r1 = T(-2) * (q1 - val) * w1 * i1;
+  const T r2 = T(-2) * (q2 - val) * w2 * i2;
   // dbeta_m/dv = 13/6 s_m ds_m + 1/2 t_m dt_m
   const T u0 = T(13.0 / 6.0) * s0, p0 = T(0.5) * t0;
   const T u1 = T(13.0 / 6.0) * s1, p1 = T(0.5) * t1;
@@ -68,151 +72,238 @@ __device__ __forceinline__ T weno5_value_grad(const T (&v)[5], T (&dv)[5]) {
   return val;
 }
 
-__device__ __forceinline__ void atomic_add_t(float* p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_add_t(double* p, double v) { atomicAdd(p, v); }
+// Adjoint of one face flux F = alpha (v+ + v-) + kappa (c_0 - c_1) (face between stencil
+// positions 2 and 3 of the six values c[0..5], w[0..5] = velocity / alpha): dc[k] =
+// lamF dF/dc_k and dw[k] = lamF dF/dw_k (w the physical face-normal velocity).  With
+// h = (w/alpha +- 1) c / 2 (scaled by 1/alpha), dF/dh = alpha dv, dh/dc = (w/alpha +- 1)/2
+// and dF/dw = dv c / 2.
+template <typename T>
+__device__ __forceinline__ void face_adjoint(const T (&cv)[6], const T (&wv)[6], T alpha, T kappa, T lamF,
+                                             T (&dc)[6], T (&dw)[6]) {
+  T hp[5], hm[5], gp[5], gm[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    hp[k] = T(0.5) * (wv[k] + T(1)) * cv[k];          // h+ at stencil k
+    hm[k] = T(0.5) * (wv[5 - k] - T(1)) * cv[5 - k];  // h- mirrored: stencil 5..1
+  }
+  weno5_value_grad<T>(hp, gp);
+  weno5_value_grad<T>(hm, gm);
+  const T la = lamF * alpha, lh = T(0.5) * lamF;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    dc[k] = T(0);
+    dw[k] = T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    dc[k] += la * gp[k] * T(0.5) * (wv[k] + T(1));
+    dw[k] += lh * gp[k] * cv[k];
+    dc[5 - k] += la * gm[k] * T(0.5) * (wv[5 - k] - T(1));
+    dw[5 - k] += lh * gm[k] * cv[5 - k];
+  }
+  dc[2] += lamF * kappa;
+  dc[3] -= lamF * kappa;
+}
 
-// Adjoint of SSP-RK3 stage STAGE of the transport, one node per thread.
-//   STAGE 3: c' = 1/3 c + 2/3 (c2 + L(c2)):  lamL = 2/3 mu, scatter into lc2;
-//   STAGE 2: c2 = 3/4 c + 1/4 (c1 + L(c1)):  lamL = 1/4 lc2, scatter into lc1; direct
-//            terms lc1 += 1/4 lc2, lc += 3/4 lc2;
-//   STAGE 1: c1 = c + L(c):                  lamL = lc1, scatter into lc; lc += lc1.
-// The thread of node i handles the faces on its + side along x and along y: for each, the
-// adjoint of the face flux lamF = lamL[i+1] - lamL[i] times the flux derivatives with
-// respect to the six stencil values of c and of the velocity, added with atomics (the
-// node's own entry merged into one add).  The floor face below row 0 (F = -Vs c) and the
-// deposit's RK3 b-weights (c/6 + c1/6 + 2 c2/3 on the floor, times Vs) give the Vs adjoint.
+// Per-face derivative records of one stage (scratch, [k][node] layout, k = stencil
+// position 0..5 of the face node + 1/2): dcx/dwx for the face on the +x side of each
+// node, dcy/dwy for the +y side (zero on the lid row).  dw is the derivative with
+// respect to the physical face-normal velocity w at that stencil position.
+template <typename T>
+struct FaceRecords {
+  T* dcx;
+  T* dwx;
+  T* dcy;
+  T* dwy;
+};
+
+constexpr int kAdjThreads = 128;
+
+// Adjoint of SSP-RK3 stage STAGE of the transport, part 1: every face once.
+//   STAGE 3: c' = 1/3 c + 2/3 (c2 + L(c2)):  lamL = 2/3 mu
+//   STAGE 2: c2 = 3/4 c + 1/4 (c1 + L(c1)):  lamL = 1/4 lc2
+//   STAGE 1: c1 = c + L(c):                  lamL = lc1
+// The thread of node i records, for the faces on its +x and +y sides, lamF = lamL[next] -
+// lamL[i] (the face flux leaves i and enters next) times the flux derivatives with respect
+// to the six stencil values of c and of w (WENO5-JS nonlinear weights included; ghost rows
+// mirror c and flip u).  The Vs terms go to a per-CTA partial: -lamF dF/dw on vertical
+// faces (w = +-u - Vs), the floor face F = -Vs c_0, and the deposit's RK3 b-weights
+// (2/3, 1/6, 1/6 of c2, c1, c on the floor).
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(128) adj_stage_kernel(Args<T> a, AdjFields<T> f) {
-  __shared__ double sh[4];
+__global__ void __launch_bounds__(kAdjThreads) adj_faces_kernel(Args<T> a, AdjFields<T> f, FaceRecords<T> fr) {
+  __shared__ double red[kAdjThreads / 32];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   const int nx = a.nx, ny = a.ny;
   const T* __restrict__ cs = STAGE == 3 ? a.c2 : (STAGE == 2 ? a.c1 : a.c);
-  const T* lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
+  const T* __restrict__ lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
   const T lscale = STAGE == 3 ? T(2.0 / 3.0) : (STAGE == 2 ? T(0.25) : T(1));
-  T* lam_cs = STAGE == 3 ? f.lc2 : (STAGE == 2 ? f.lc1 : f.lc);
   double vs_acc = 0.0;
   if (x < nx) {
     const long long n = a.n;
     const long long node = (long long)y * nx + x;
-    const T alpha = a.alpha, ia = a.inv_alpha;
+    const T alpha = a.alpha, ia = a.inv_alpha, kappa = a.kappa, vs = a.vs;
     const T lam_here = lscale * lsrc[node];
-    T own = T(0);  // everything this thread adds to lam_cs[node]
-    if (STAGE == 2) {
-      own = lam_here;                 // 1/4 lc2: c1 enters c2 directly
-      f.lc[node] += T(3) * lam_here;  // 3/4 lc2: c^n enters c2 (no other writer of lc here)
-    } else if (STAGE == 1) {
-      own = lam_here;                 // lc1: c^n enters c1 directly
-    }
-    for (int d = 0; d < 2; ++d) {
-      const bool vert = d == 1;
-      if (vert && y == ny - 1) continue;  // lid: no flux
-      const long long next = vert ? node + nx : (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
-      const T lamF = lscale * lsrc[next] - lam_here;  // F_{+1/2} leaves node, enters next
-      long long idx[6];
-      bool ghost[6];
-      T cv[6], wv[6];
-#pragma unroll
-      for (int k = -2; k <= 3; ++k) {
-        int p = (vert ? y : x) + k;
-        bool g = false;
-        if (vert) {
-          if (p < 0) {
-            p = -1 - p;
-            g = true;
-          } else if (p >= ny) {
-            p = 2 * ny - 1 - p;
-            g = true;
-          }
-          idx[k + 2] = (long long)p * nx + x;
-        } else {
-          p = p < 0 ? p + nx : (p >= nx ? p - nx : p);
-          idx[k + 2] = (long long)y * nx + p;
-        }
-        ghost[k + 2] = g;
-        cv[k + 2] = cs[idx[k + 2]];
-        T ud = a.u[(long long)d * n + idx[k + 2]];
-        if (g) ud = -ud;
-        wv[k + 2] = (ud - (vert ? a.vs : T(0))) * ia;  // w / alpha
-      }
-      T hp[5], hm[5], gp[5], gm[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        hp[k] = T(0.5) * (wv[k] + T(1)) * cv[k];          // h+ at stencil k-2
-        hm[k] = T(0.5) * (wv[5 - k] - T(1)) * cv[5 - k];  // h- mirrored: stencil 3..-1
-      }
-      weno5_value_grad<T>(hp, gp);
-      weno5_value_grad<T>(hm, gm);
-      // F = alpha (v+ + v-) + kappa (c_0 - c_1): dF/dh = alpha dv; dh/dc = (w/alpha +- 1)/2,
-      // dF/dw_phys = dv c / 2
-      T dFdc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-      T dFdw[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        dFdc[k] += alpha * gp[k] * T(0.5) * (wv[k] + T(1));
-        dFdw[k] += gp[k] * T(0.5) * cv[k];
-        dFdc[5 - k] += alpha * gm[k] * T(0.5) * (wv[5 - k] - T(1));
-        dFdw[5 - k] += gm[k] * T(0.5) * cv[5 - k];
-      }
-      dFdc[2] += a.kappa;
-      dFdc[3] -= a.kappa;
+    // +x face (periodic)
+    {
+      T cv[6], wv[6], dc[6], dw[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        if (k == 2)  // the node itself (never a ghost: y is inside the lattice)
-          own += lamF * dFdc[k];
-        else
-          atomic_add_t(lam_cs + idx[k], lamF * dFdc[k]);
-        const T du = ghost[k] ? -dFdw[k] : dFdw[k];  // w = +-u - Vs (vertical) or u (horizontal)
-        atomic_add_t(f.lam_u + (long long)d * n + idx[k], lamF * du);
-        if (vert) vs_acc -= (double)(lamF * dFdw[k]);
+        const int p = wrap_any(x - 2 + k, nx);
+        cv[k] = cs[(long long)y * nx + p];
+        wv[k] = a.u[(long long)y * nx + p] * ia;
+      }
+      const T lamF = lscale * lsrc[(long long)y * nx + (x + 1 == nx ? 0 : x + 1)] - lam_here;
+      face_adjoint<T>(cv, wv, alpha, kappa, lamF, dc, dw);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        fr.dcx[k * n + node] = dc[k];
+        fr.dwx[k * n + node] = dw[k];
+      }
+    }
+    // +y face (none on the lid row)
+    if (y < ny - 1) {
+      T cv[6], wv[6], dc[6], dw[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int p = y - 2 + k;
+        const bool ghost = p < 0 || p >= ny;
+        const int pr = p < 0 ? -1 - p : (p >= ny ? 2 * ny - 1 - p : p);
+        const long long q = (long long)pr * nx + x;
+        cv[k] = cs[q];
+        const T u = a.u[n + q];
+        wv[k] = ((ghost ? -u : u) - vs) * ia;
+      }
+      const T lamF = lscale * lsrc[node + nx] - lam_here;
+      face_adjoint<T>(cv, wv, alpha, kappa, lamF, dc, dw);
+      T sw = T(0);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        fr.dcy[k * n + node] = dc[k];
+        fr.dwy[k * n + node] = dw[k];
+        sw += dw[k];
+      }
+      vs_acc -= (double)sw;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        fr.dcy[k * n + node] = T(0);
+        fr.dwy[k * n + node] = T(0);
       }
     }
     if (y == 0) {
-      own -= a.vs * lam_here;  // floor face below row 0: F = -Vs c_0 enters L_0 with +
-      vs_acc -= (double)(cs[node] * lam_here);
-      vs_acc += (double)cs[node] * (STAGE == 3 ? 2.0 / 3.0 : 1.0 / 6.0);  // deposit b-weights
+      const T c0 = cs[node];
+      vs_acc += (double)c0 * (STAGE == 3 ? 2.0 / 3.0 : 1.0 / 6.0) - (double)(c0 * lam_here);
     }
-    atomic_add_t(lam_cs + node, own);
   }
-  // block sum of the Vs adjoint, one double atomic per block
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) vs_acc += __shfl_down_sync(0xffffffffu, vs_acc, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = vs_acc;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vs_acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    if (s != 0.0) atomicAdd(f.lam_vs, s);
+    for (int w = 0; w < kAdjThreads / 32; ++w) s += red[w];
+    f.vs_part[blockIdx.y * gridDim.x + blockIdx.x] += s;  // own slot, fixed order over steps
   }
 }
 
-// Seed the accumulators of a reverse step at node k from m = lambda(c') there: the
-// direct terms 2/3 m (into lc2) and 1/3 m (into lc), and the floor terms of the deposit.
-template <typename T>
-__device__ __forceinline__ void adj_seed(const AdjFields<T>& f, long long k, bool floor, T m, T vs) {
-  f.lc2[k] = T(2.0 / 3.0) * m + (floor ? T(2.0 / 3.0) * vs : T(0));
-  f.lc1[k] = floor ? vs / T(6) : T(0);
-  f.lc[k] = T(1.0 / 3.0) * m + (floor ? vs / T(6) : T(0));
+// Part 2: each node gathers the records of the faces whose stencils contain it (x faces
+// x + 2 - k at position k, periodic; y faces y + 2 - k for existing faces, plus the ghost
+// positions that mirror onto rows 0, 1, ny - 2, ny - 1, with u odd) and writes
+//   STAGE 3: lc2 = lamL + L^T lamL
+//   STAGE 2: lc1 = lamL + L^T lamL
+//   STAGE 1: lc  = 1/3 mu + 3/4 lc2 + lamL + L^T lamL
+// with the deposit's floor terms and the floor face, and lambda(u) (written by stage 3,
+// accumulated by stages 2 and 1).
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(kAdjThreads) adj_gather_kernel(Args<T> a, AdjFields<T> f, FaceRecords<T> fr) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (x >= nx) return;
+  const long long n = a.n;
+  const long long node = (long long)y * nx + x;
+  const T* __restrict__ lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
+  const T lscale = STAGE == 3 ? T(2.0 / 3.0) : (STAGE == 2 ? T(0.25) : T(1));
+  T* __restrict__ lam_cs = STAGE == 3 ? f.lc2 : (STAGE == 2 ? f.lc1 : f.lc);
+  const T vs = a.vs;
+  T gc = T(0), gx = T(0), gy = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const long long q = (long long)y * nx + wrap_any(x + 2 - k, nx);
+    gc += fr.dcx[k * n + q];
+    gx += fr.dwx[k * n + q];
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int yf = y + 2 - k;
+    if (yf >= 0 && yf <= ny - 2) {
+      const long long q = (long long)yf * nx + x;
+      gc += fr.dcy[k * n + q];
+      gy += fr.dwy[k * n + q];
+    }
+  }
+  // ghost stencil positions folded onto the mirror rows (p = -1 -> 0, -2 -> 1, ny -> ny-1,
+  // ny+1 -> ny-2); face yf has position p at k = p - yf + 2
+  auto ghost = [&](int yf, int k) {
+    const long long q = (long long)yf * nx + x;
+    gc += fr.dcy[k * n + q];
+    gy -= fr.dwy[k * n + q];
+  };
+  if (y == 0) {
+    ghost(0, 1);
+    if (ny - 2 >= 1) ghost(1, 0);
+  }
+  if (y == 1) ghost(0, 0);
+  if (y == ny - 1) {
+    ghost(ny - 2, 4);
+    if (ny - 3 >= 0) ghost(ny - 3, 5);
+  }
+  if (y == ny - 2) ghost(ny - 2, 5);
+  const T lam_here = lscale * lsrc[node];
+  T v = lam_here + gc;
+  if (STAGE == 1) v += T(1.0 / 3.0) * f.mu[node] + T(0.75) * f.lc2[node];
+  if (y == 0) {
+    v += (STAGE == 3 ? T(2.0 / 3.0) : T(1.0 / 6.0)) * vs;  // deposit b-weight
+    v -= vs * lam_here;                                    // floor face
+  }
+  lam_cs[node] = v;
+  if (STAGE == 3) {
+    f.lam_u[node] = gx;
+    f.lam_u[n + node] = gy;
+  } else {
+    f.lam_u[node] += gx;
+    f.lam_u[n + node] += gy;
+  }
 }
 
-// State before the last reverse step: J does not depend on c^N or the final populations,
-// so mu = 0 and lambda(u) = 0.
+// State before the last reverse step: J does not depend on c^N or the final populations.
 template <typename T>
-__global__ void adj_init_kernel(AdjFields<T> f, long long n, int nx, T vs) {
+__global__ void adj_init_kernel(AdjFields<T> f, long long n, int nparts) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  f.mu[k] = T(0);
-  adj_seed<T>(f, k, k < nx, T(0), vs);
-  f.lam_u[k] = T(0);
-  f.lam_u[n + k] = T(0);
-  if (k == 0) *f.lam_vs = 0.0;
+  if (k < n) f.mu[k] = T(0);
+  if (k < nparts) f.vs_part[k] = 0.0;
+}
+
+// dJ/dVs = sum of the per-CTA partials in index order (one block).
+__global__ void adj_vs_finish_kernel(const double* part, int nparts, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[k];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) tot += sh[k];
+    *out = tot;
+  }
 }
 
 // Adjoint of the fluid step at each node.  Inputs: the populations of step n (AA layout
 // with its parity), c^n, lambda of the streamed populations of step n+1 (natural layout
 // lam_next[i][node]), lambda(u) and the transport part of lambda(c^n) in lc.  Outputs:
 // lambda of the populations of step n (natural layout) and lambda(c^n) = lc - A
-// lambda(F_y) in mu; then seeds lc2, lc1, lc for the step before and zeroes lambda(u).
+// lambda(F_y) in mu.
 template <typename T, int PARITY>
 __global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, AdjFields<T> f, const T* lam_next,
                                                         T* lam_out) {
@@ -267,11 +358,7 @@ __global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, AdjFields<T> 
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     lam_out[i * n + node] = keep * mu[i] + lam_drho + ljx * T(D2Q9::cx(i)) + ljy * T(D2Q9::cy(i));
-  const T lam_c = f.lc[node] - a.A * lFy;
-  f.mu[node] = lam_c;
-  adj_seed<T>(f, node, y == 0, lam_c, a.vs);
-  f.lam_u[node] = T(0);
-  f.lam_u[n + node] = T(0);
+  f.mu[node] = f.lc[node] - a.A * lFy;
 }
 
 }  // namespace lw

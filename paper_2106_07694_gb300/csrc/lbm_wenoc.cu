@@ -934,7 +934,8 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
 // Adjoint workspace: a checkpoint (populations + c, the handle's layout from g to c) at
 // the start of every segment; one segment of step records (the handle's layout from g to
 // u: populations and c before the step, c1, c2 and u of the step); lambda of the
-// populations (two buffers, natural layout); mu, lc2, lc1, lc, lambda(u); lambda(Vs).
+// populations (two buffers, natural layout); mu, lc2, lc1, lc, lambda(u); lambda(Vs) and
+// its per-CTA partials; the face derivative records of one stage (24 fields).
 
 namespace {
 
@@ -943,7 +944,8 @@ bool gradient_params_ok(const lbm_wenoc* h) {
 }
 
 struct GradLayout {
-  size_t ckpt, rec, lg0, lg1, mu, lc2, lc1, lc, lu, vs, total;
+  size_t ckpt, rec, lg0, lg1, mu, lc2, lc1, lc, lu, vs, vs_part, faces, total;
+  int nparts;  // per-CTA dJ/dVs partials of the face kernel
   size_t ckpt_bytes, rec_bytes;  // one checkpoint, one step record
   int64_t nseg;
 };
@@ -962,7 +964,7 @@ GradLayout grad_layout(const lbm_wenoc_params& p, int64_t nsteps, int32_t segmen
     off = align_up(off + bytes, 256);
     return o;
   };
-  G.ckpt = take(G.ckpt_bytes * (size_t)G.nseg);
+  G.ckpt = take(G.ckpt_bytes * (size_t)(G.nseg - 1));  // the last segment is recorded directly
   G.rec = take(G.rec_bytes * (size_t)segment);
   G.lg0 = take(9 * n * es);
   G.lg1 = take(9 * n * es);
@@ -972,6 +974,9 @@ GradLayout grad_layout(const lbm_wenoc_params& p, int64_t nsteps, int32_t segmen
   G.lc = take(n * es);
   G.lu = take(2 * n * es);
   G.vs = take(sizeof(double) * 4);
+  G.nparts = ((p.nx + lw::kAdjThreads - 1) / lw::kAdjThreads) * p.ny;
+  G.vs_part = take(sizeof(double) * (size_t)G.nparts);
+  G.faces = take(24 * n * es);
   G.total = off;
   return G;
 }
@@ -983,8 +988,8 @@ int copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 // Reverse step over the step record `rec` (populations with parity par): mu = lambda(c^{n+1})
 // in, lambda(c^n) out; lam_next / lam_out = lambda of the populations of steps n+1 / n.
 template <typename T>
-int adjoint_step(lbm_wenoc* h, int par, const unsigned char* rec, const lw::AdjFields<T>& f, const T* lam_next,
-                 T* lam_out) {
+int adjoint_step(lbm_wenoc* h, int par, const unsigned char* rec, const lw::AdjFields<T>& f,
+                 const lw::FaceRecords<T>& fr, const T* lam_next, T* lam_out) {
   Args<T> a = make_args<T>(h);
   const Layout& L = h->L;
   unsigned char* r = const_cast<unsigned char*>(rec);
@@ -995,14 +1000,17 @@ int adjoint_step(lbm_wenoc* h, int par, const unsigned char* rec, const lw::AdjF
   a.u = reinterpret_cast<T*>(r + (L.u - L.g));
   cudaStream_t s = h->stream;
   const dim3 blk(kLbmThreads), grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, 1);
-  lw::adj_stage_kernel<T, 3><<<grd, blk, 0, s>>>(a, f);
-  lw::adj_stage_kernel<T, 2><<<grd, blk, 0, s>>>(a, f);
-  lw::adj_stage_kernel<T, 1><<<grd, blk, 0, s>>>(a, f);
+  lw::adj_faces_kernel<T, 3><<<grd, blk, 0, s>>>(a, f, fr);
+  lw::adj_gather_kernel<T, 3><<<grd, blk, 0, s>>>(a, f, fr);
+  lw::adj_faces_kernel<T, 2><<<grd, blk, 0, s>>>(a, f, fr);
+  lw::adj_gather_kernel<T, 2><<<grd, blk, 0, s>>>(a, f, fr);
+  lw::adj_faces_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, fr);
+  lw::adj_gather_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, fr);
   if (par == 0)
     lw::adj_fluid_kernel<T, 0><<<grd, blk, 0, s>>>(a, f, lam_next, lam_out);
   else
     lw::adj_fluid_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, lam_next, lam_out);
-  h->launches += 4;
+  h->launches += 7;
   return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
@@ -1014,16 +1022,36 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   cudaStream_t s = h->stream;
   const Layout& L = h->L;
   unsigned char* state = h->ws + L.g;
-  // forward, keeping the state at the start of every segment
+  const size_t n = (size_t)h->n;
+  std::vector<int> rec_parity((size_t)segment);
+  // run the steps of one segment, recording each (populations and c before the step, then
+  // the step's c1, c2 and u)
+  auto record_segment = [&](int64_t len) -> int {
+    for (int64_t k = 0; k < len; ++k) {
+      unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
+      rec_parity[(size_t)k] = h->parity;
+      int r = copy_d2d(rec, state, G.ckpt_bytes, s);
+      if (r == LW_OK) r = lbm_wenoc_step(h, 1);
+      if (r == LW_OK) r = copy_d2d(rec + (L.c1 - L.g), h->ws + L.c1, L.u + 2 * n * sizeof(T) - L.c1, s);
+      if (r != LW_OK) return r;
+    }
+    return LW_OK;
+  };
+  // forward, keeping the state at the start of every segment; the last segment is
+  // recorded on the way (it is the first one the reverse sweep needs)
   std::vector<int> ck_parity((size_t)G.nseg);
   for (int64_t sg = 0; sg < G.nseg; ++sg) {
     const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
     ck_parity[(size_t)sg] = h->parity;
-    if ((rc = copy_d2d(aw + G.ckpt + (size_t)sg * G.ckpt_bytes, state, G.ckpt_bytes, s)) != LW_OK) return rc;
-    if ((rc = lbm_wenoc_step(h, len)) != LW_OK) return rc;
+    if (sg == G.nseg - 1) {
+      rc = record_segment(len);
+    } else {
+      rc = copy_d2d(aw + G.ckpt + (size_t)sg * G.ckpt_bytes, state, G.ckpt_bytes, s);
+      if (rc == LW_OK) rc = lbm_wenoc_step(h, len);
+    }
+    if (rc != LW_OK) return rc;
   }
   if ((rc = lbm_wenoc_deposited_mass(h, J)) != LW_OK) return rc;
-  const size_t n = (size_t)h->n;
   lw::AdjFields<T> f;
   f.mu = reinterpret_cast<T*>(aw + G.mu);
   f.lc2 = reinterpret_cast<T*>(aw + G.lc2);
@@ -1031,33 +1059,36 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   f.lc = reinterpret_cast<T*>(aw + G.lc);
   f.lam_u = reinterpret_cast<T*>(aw + G.lu);
   f.lam_vs = reinterpret_cast<double*>(aw + G.vs);
+  f.vs_part = reinterpret_cast<double*>(aw + G.vs_part);
+  const int nparts = G.nparts;
+  lw::FaceRecords<T> fr;
+  fr.dcx = reinterpret_cast<T*>(aw + G.faces);
+  fr.dwx = fr.dcx + 6 * n;
+  fr.dcy = fr.dcx + 12 * n;
+  fr.dwy = fr.dcx + 18 * n;
   T* lg[2] = {reinterpret_cast<T*>(aw + G.lg0), reinterpret_cast<T*>(aw + G.lg1)};
   if (cudaMemsetAsync(lg[0], 0, 9 * n * sizeof(T), s) != cudaSuccess) return LW_ECUDA;
-  lw::adj_init_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, (long long)n, h->p.nx, (T)h->p.settling_velocity);
+  lw::adj_init_kernel<T><<<(unsigned)((std::max<size_t>(n, (size_t)nparts) + 255) / 256), 256, 0, s>>>(
+      f, (long long)n, nparts);
   h->launches += 1;
   int cur = 0;
-  std::vector<int> rec_parity((size_t)segment);
   for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
     const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
-    // recompute the segment from its checkpoint, recording every step
-    if ((rc = copy_d2d(state, aw + G.ckpt + (size_t)sg * G.ckpt_bytes, G.ckpt_bytes, s)) != LW_OK) return rc;
-    h->parity = ck_parity[(size_t)sg];
-    h->cur = 0;
-    for (int64_t k = 0; k < len; ++k) {
-      unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
-      rec_parity[(size_t)k] = h->parity;
-      if ((rc = copy_d2d(rec, state, G.ckpt_bytes, s)) != LW_OK) return rc;  // populations, c^n
-      if ((rc = lbm_wenoc_step(h, 1)) != LW_OK) return rc;
-      if ((rc = copy_d2d(rec + (L.c1 - L.g), h->ws + L.c1, L.u + 2 * n * sizeof(T) - L.c1, s)) != LW_OK)
-        return rc;  // c1, c2, u of the step
+    if (sg != G.nseg - 1) {  // recompute the segment from its checkpoint
+      if ((rc = copy_d2d(state, aw + G.ckpt + (size_t)sg * G.ckpt_bytes, G.ckpt_bytes, s)) != LW_OK) return rc;
+      h->parity = ck_parity[(size_t)sg];
+      h->cur = 0;
+      if ((rc = record_segment(len)) != LW_OK) return rc;
     }
     for (int64_t k = len - 1; k >= 0; --k) {
       const unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
-      if ((rc = adjoint_step<T>(h, rec_parity[(size_t)k], rec, f, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
+      if ((rc = adjoint_step<T>(h, rec_parity[(size_t)k], rec, f, fr, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
       cur ^= 1;
     }
   }
   // mu now holds lambda(c^0)
+  lw::adj_vs_finish_kernel<<<1, 256, 0, s>>>(f.vs_part, nparts, f.lam_vs);
+  h->launches += 1;
   cudaMemcpyKind k = is_device_pointer(grad_c0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (cudaMemcpyAsync(grad_c0, f.mu, n * sizeof(T), k, s) != cudaSuccess) return LW_ECUDA;
   if (cudaMemcpyAsync(dJ_dVs, f.lam_vs, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LW_ECUDA;
