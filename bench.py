@@ -37,6 +37,20 @@ BATCH_METRIC = "coupled LBM+WENO5 GLUPS, batched sweep of 64 D2Q9 FP32 instances
 UNIT = "GLUPS"
 
 
+# flops per node of one adj_faces launch, counted on the formulation: per WENO5 value and
+# its five partial derivatives 131 (candidates 15, differences 21, indicators 15 + 3
+# reciprocals, weights 12, value 5, sensitivity factors 18, derivatives 42), per face two
+# of them + split values 30 + derivative assembly 74 = 366, two faces per node + scaled
+# velocities and face adjoints 34
+ADJ_FACES_FLOP = 766
+
+
+def fp32_peak_tflops(clk):
+    """FP32 ALU peak derived from the unit counts: 152 SMs x 128 lanes x 2 flop x SM clock."""
+    sm_hz = ((clk or {}).get("sm_mhz") or 2070.0) * 1e6
+    return 152 * 128 * 2 * sm_hz / 1e12
+
+
 def phys_kwargs(wl):
     return dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
                 settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity)
@@ -474,7 +488,27 @@ def bench_adjoint(args):
     t0 = time.perf_counter()
     e2e_call()
     e2e_s = time.perf_counter() - t0
+    # the same gradient with every step recorded in HBM (no checkpoints, no recompute)
+    nb_all = lw.lbm_wenoc_gradient_workspace_bytes(sim.params, nsteps, nsteps)
+    adj_all = torch.empty(nb_all, dtype=torch.uint8, device="cuda")
+    lw.lbm_wenoc_deposit_gradient(sim.handle, c0, nsteps, nsteps, adj_all, nb_all, grad)
+    torch.cuda.synchronize()
+    e0.record()
+    J_all, dvs_all = lw.lbm_wenoc_deposit_gradient(sim.handle, c0, nsteps, nsteps, adj_all, nb_all, grad)
+    e1.record()
+    torch.cuda.synchronize()
+    all_ms = e0.elapsed_time(e1)
+    del adj_all
+    # per-kernel averages: one more gradient call with an event pair around every launch
+    lw.lbm_wenoc_profile_enable(sim.handle, True)
+    lw.lbm_wenoc_profile_read(sim.handle, reset=True)
+    lw.lbm_wenoc_deposit_gradient(sim.handle, c0, nsteps, seg, adj, nbytes, grad)
+    prof = lw.lbm_wenoc_profile_read(sim.handle, reset=True)
+    lw.lbm_wenoc_profile_enable(sim.handle, False)
+    kernels = {k: {"launches": c, "avg_us": 1e3 * ms / c, "total_ms": ms} for k, (c, ms) in prof.items() if c}
     nodes = wl.nodes
+    peak_alu = fp32_peak_tflops(clk)
+    faces_us = kernels.get("adj_faces", {}).get("avg_us")
     value = nodes * nsteps / (grad_ms * 1e-3) / 1e9
     line = {
         "metric": ADJOINT_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
@@ -484,7 +518,16 @@ def bench_adjoint(args):
                    "adjoint_workspace_bytes": nbytes, "l2": "working set > L2 (states of one segment)"},
         "forward": {"ms": fwd_ms, "glups": nodes * nsteps / (fwd_ms * 1e-3) / 1e9},
         "gradient_over_forward": grad_ms / fwd_ms,
+        "no_recompute": {"ms_per_step": all_ms / nsteps, "gradient_over_forward": all_ms / fwd_ms,
+                         "adjoint_workspace_bytes": nb_all, "same_result": bool(J_all == J and dvs_all == dvs),
+                         "note": "all step records kept in HBM instead of a checkpoint every 100 steps"},
         "J": J, "dJ_dVs": dvs, "grad_l2": float(torch.linalg.vector_norm(grad.double())),
+        "kernels": kernels,
+        "roofline": None if not faces_us else {
+            "kernel": "adj_faces", "bound": "alu", "alg_flop_per_node": ADJ_FACES_FLOP,
+            "achieved": ADJ_FACES_FLOP * nodes / (faces_us * 1e-6) / 1e12, "peak": peak_alu,
+            "unit": "TFLOP/s", "frac": ADJ_FACES_FLOP * nodes / (faces_us * 1e-6) / 1e12 / peak_alu,
+            "traffic": None},
         "e2e": {"value": nodes * nsteps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * nodes / nsteps,
                 "d2h_bytes_per_step": (4 * nodes + 8) / nsteps},
         "gpu_launches": int(launches), "clocks": clk,

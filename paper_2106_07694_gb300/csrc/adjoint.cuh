@@ -5,15 +5,16 @@
 //   u = U(g, c); g' = Stream(Collide(g, F(c)));
 //   c1 = c + L(c; u); c2 = 3/4 c + 1/4 c1 + 1/4 L(c1; u); c' = 1/3 c + 2/3 c2 + 2/3 L(c2; u);
 //   J += Vs sum_floor(c/6 + c1/6 + 2 c2/3).
-// Given lambda(c') and lambda(g') and the stored u, c1, c2 of the step, one reverse step
-// is seven launches: the three transport stages backwards (for each, adj_faces_kernel
-// records every face's flux derivatives once and adj_gather_kernel sums, per node, the
-// records of the faces whose stencils contain it: the Jacobian-transpose of L with respect
-// to its input and to u, WENO5-JS nonlinear weights included), then the fluid step backwards (adj_fluid_kernel: reverse
-// streaming with bounce-back, transpose of the BGK-Guo collision, the velocity chain
-// u = (j + F/2)/rho, the buoyancy F_y = -A c).  The Lax-Friedrichs alpha is a fixed
-// parameter here (the caller sets lf_alpha), so d/dVs holds alpha fixed.  No atomics: results are
-// bitwise reproducible and independent of the checkpoint spacing.
+// Given lambda(c') and lambda(g') and the recorded c, c1, c2, u, rho of the step, one
+// reverse step is six launches: the three transport stages backwards (for each,
+// adj_faces_kernel records every face's flux derivatives once and a gather sums, per node,
+// the records of the faces whose stencils contain it: the Jacobian-transpose of L with
+// respect to its input and to u, WENO5-JS nonlinear weights included), the last gather
+// fused with the fluid step backwards (reverse streaming with bounce-back, transpose of
+// the BGK-Guo collision, the velocity chain u = (j + F/2)/rho, the buoyancy F_y = -A c).
+// The Lax-Friedrichs alpha is a fixed parameter here (the caller sets lf_alpha), so d/dVs
+// holds alpha fixed.  No atomics: results are bitwise reproducible and independent of the
+// checkpoint spacing.
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
@@ -36,6 +37,10 @@ struct AdjFields {
   double* vs_part;  // per-CTA partial sums of dJ/dVs, accumulated over stages and steps
 };
 
+// Reciprocal for the derivative weights: MUFU reciprocal (2 ulp) in FP32, exact in FP64.
+__device__ __forceinline__ float adj_rcp(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double adj_rcp(double x) { return 1.0 / x; }
+
 // WENO5-JS face value of the scaled values v[0..4] (upwind side first) and its partial
 // derivatives dv[0..4]: sum_k w_k dq_k/dv_j + sum_m (q_m - val) w_m (-2/(eps+beta_m)) dbeta_m/dv_j.
 template <typename T>
@@ -47,12 +52,12 @@ __device__ __forceinline__ T weno5_value_grad(const T (&v)[5], T (&dv)[5]) {
   const T q2 = (T(2) * c + T(5) * d - e) * sixth;
   const T s0 = a - T(2) * b + c, s1 = b - T(2) * c + d, s2 = c - T(2) * d + e;
   const T t0 = a - T(4) * b + T(3) * c, t1 = b - d, t2 = T(3) * c - T(4) * d + e;
-  // reciprocals of eps + beta_m: four divisions in all
-  const T i0 = T(1) / (eps + T(13.0 / 12.0) * s0 * s0 + T(0.25) * t0 * t0);
-  const T i1 = T(1) / (eps + T(13.0 / 12.0) * s1 * s1 + T(0.25) * t1 * t1);
-  const T i2 = T(1) / (eps + T(13.0 / 12.0) * s2 * s2 + T(0.25) * t2 * t2);
+  // reciprocals of eps + beta_m and of the weight sum: four in all
+  const T i0 = adj_rcp(eps + T(13.0 / 12.0) * s0 * s0 + T(0.25) * t0 * t0);
+  const T i1 = adj_rcp(eps + T(13.0 / 12.0) * s1 * s1 + T(0.25) * t1 * t1);
+  const T i2 = adj_rcp(eps + T(13.0 / 12.0) * s2 * s2 + T(0.25) * t2 * t2);
   const T a0 = T(0.1) * i0 * i0, a1 = T(0.6) * i1 * i1, a2 = T(0.3) * i2 * i2;
-  const T inv = T(1) / (a0 + a1 + a2);
+  const T inv = adj_rcp(a0 + a1 + a2);
   const T w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
   const T val = w0 * q0 + w1 * q1 + w2 * q2;
   // weight-sensitivity factors r_m = (q_m - val) w_m (-2 / (eps + beta_m))
@@ -209,25 +214,24 @@ __global__ void __launch_bounds__(kAdjThreads) adj_faces_kernel(Args<T> a, AdjFi
 
 // Part 2: each node gathers the records of the faces whose stencils contain it (x faces
 // x + 2 - k at position k, periodic; y faces y + 2 - k for existing faces, plus the ghost
-// positions that mirror onto rows 0, 1, ny - 2, ny - 1, with u odd) and writes
+// positions that mirror onto rows 0, 1, ny - 2, ny - 1, with u odd):
 //   STAGE 3: lc2 = lamL + L^T lamL
 //   STAGE 2: lc1 = lamL + L^T lamL
 //   STAGE 1: lc  = 1/3 mu + 3/4 lc2 + lamL + L^T lamL
-// with the deposit's floor terms and the floor face, and lambda(u) (written by stage 3,
-// accumulated by stages 2 and 1).
+// with the deposit's floor terms and the floor face; gx, gy = this stage's part of
+// lambda(u).
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(kAdjThreads) adj_gather_kernel(Args<T> a, AdjFields<T> f, FaceRecords<T> fr) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
+__device__ __forceinline__ void gather_node(const Args<T>& a, const AdjFields<T>& f, const FaceRecords<T>& fr,
+                                            int x, int y, T& v, T& gx, T& gy) {
   const int nx = a.nx, ny = a.ny;
-  if (x >= nx) return;
   const long long n = a.n;
   const long long node = (long long)y * nx + x;
   const T* __restrict__ lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
   const T lscale = STAGE == 3 ? T(2.0 / 3.0) : (STAGE == 2 ? T(0.25) : T(1));
-  T* __restrict__ lam_cs = STAGE == 3 ? f.lc2 : (STAGE == 2 ? f.lc1 : f.lc);
   const T vs = a.vs;
-  T gc = T(0), gx = T(0), gy = T(0);
+  T gc = T(0);
+  gx = T(0);
+  gy = T(0);
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const long long q = (long long)y * nx + wrap_any(x + 2 - k, nx);
@@ -261,13 +265,25 @@ __global__ void __launch_bounds__(kAdjThreads) adj_gather_kernel(Args<T> a, AdjF
   }
   if (y == ny - 2) ghost(ny - 2, 5);
   const T lam_here = lscale * lsrc[node];
-  T v = lam_here + gc;
+  v = lam_here + gc;
   if (STAGE == 1) v += T(1.0 / 3.0) * f.mu[node] + T(0.75) * f.lc2[node];
   if (y == 0) {
     v += (STAGE == 3 ? T(2.0 / 3.0) : T(1.0 / 6.0)) * vs;  // deposit b-weight
     v -= vs * lam_here;                                    // floor face
   }
-  lam_cs[node] = v;
+}
+
+// Stages 3 and 2: write lc2 / lc1 and lambda(u) (written by stage 3, accumulated by 2).
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(kAdjThreads) adj_gather_kernel(Args<T> a, AdjFields<T> f, FaceRecords<T> fr) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= a.nx) return;
+  const long long n = a.n;
+  const long long node = (long long)y * a.nx + x;
+  T v, gx, gy;
+  gather_node<T, STAGE>(a, f, fr, x, y, v, gx, gy);
+  (STAGE == 3 ? f.lc2 : f.lc1)[node] = v;
   if (STAGE == 3) {
     f.lam_u[node] = gx;
     f.lam_u[n + node] = gy;
@@ -299,31 +315,26 @@ __global__ void adj_vs_finish_kernel(const double* part, int nparts, double* out
   }
 }
 
-// Adjoint of the fluid step at each node.  Inputs: the populations of step n (AA layout
-// with its parity), c^n, lambda of the streamed populations of step n+1 (natural layout
-// lam_next[i][node]), lambda(u) and the transport part of lambda(c^n) in lc.  Outputs:
-// lambda of the populations of step n (natural layout) and lambda(c^n) = lc - A
-// lambda(F_y) in mu.
-template <typename T, int PARITY>
-__global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, AdjFields<T> f, const T* lam_next,
-                                                        T* lam_out) {
+// Adjoint of the fluid step at one node, fused with the stage-1 gather (which completes
+// lambda(c^n)'s transport part lc and lambda(u) at this node).  Inputs: rho and u of step
+// n as the forward step computed them (recorded), c^n, lambda of the streamed populations
+// of step n+1 (natural layout lam_next[i][node]).  Outputs: lambda of the populations of
+// step n (natural layout) and lambda(c^n) = lc - A lambda(F_y) in mu.  The collision
+// g* = (1 - w) g + w geq(rho - 1, u) + src(u, F) and u = (j + F/2)/rho depend on the
+// populations only through rho and j.
+template <typename T>
+__global__ void __launch_bounds__(128) adj_gather_fluid_kernel(Args<T> a, AdjFields<T> f, FaceRecords<T> fr,
+                                                               const T* rho_rec, const T* lam_next, T* lam_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= a.nx) return;
   const long long n = a.n;
   const long long node = (long long)y * a.nx + x;
-  T g[9];
-  load_populations<D2Q9, T, PARITY>(a, x, y, 0, node, g);
-  T drho = T(0), jx = T(0), jy = T(0);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    drho += g[i];
-    jx += D2Q9::cx(i) * g[i];
-    jy += D2Q9::cy(i) * g[i];
-  }
+  T lc, gx, gy;
+  gather_node<T, 1>(a, f, fr, x, y, lc, gx, gy);
   const T Fx = a.bf[0], Fy = a.bf[1] - a.A * a.c[node];
-  const T rho = T(1) + drho;
-  const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho;
+  const T rho = rho_rec[node];
+  const T ux = a.u[node], uy = a.u[n + node];
   const T uu = ux * ux + uy * uy;
   // adjoint of the post-collision populations: reverse streaming with bounce-back
   T mu[9];
@@ -335,8 +346,7 @@ __global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, AdjFields<T> 
     else
       mu[i] = lam_next[D2Q9::opp(i) * n + node];
   }
-  // collision g* = (1 - w) g + w geq(drho, u) + src(u, F)
-  T lam_drho = T(0), lux = f.lam_u[node], luy = f.lam_u[n + node], lFy = T(0);
+  T lam_drho = T(0), lux = f.lam_u[node] + gx, luy = f.lam_u[n + node] + gy, lFy = T(0);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const T wi = T(D2Q9::w(i));
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(128) adj_fluid_kernel(Args<T> a, AdjFields<T> 
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     lam_out[i * n + node] = keep * mu[i] + lam_drho + ljx * T(D2Q9::cx(i)) + ljy * T(D2Q9::cy(i));
-  f.mu[node] = f.lc[node] - a.A * lFy;
+  f.mu[node] = lc - a.A * lFy;
 }
 
 }  // namespace lw

@@ -145,17 +145,23 @@ __global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
 // a row taken once per block (a block is one row segment), and streaming cache
 // hints on the population traffic (each population is touched once per step), so
 // that c and u stay in L2 for the transport kernel that follows.
-template <typename T, int PARITY>
-__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by);
+template <typename T, int PARITY, bool RHO = false>
+__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out = nullptr);
 
 template <typename T, int PARITY>
 __global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
   lbm_d2q9_body<T, PARITY>(a, blockIdx.x, blockIdx.y);
 }
 
-// Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.
+// The same step that also stores rho (the steps recorded for the adjoint).
 template <typename T, int PARITY>
-__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by) {
+__global__ void __launch_bounds__(128) lbm_d2q9_record_kernel(Args<T> a, T* rho_out) {
+  lbm_d2q9_body<T, PARITY, true>(a, blockIdx.x, blockIdx.y, rho_out);
+}
+
+// Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.
+template <typename T, int PARITY, bool RHO>
+__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out) {
   const int x = bx * blockDim.x + threadIdx.x;
   const int y = by;
   const int nx = a.nx, ny = a.ny;
@@ -203,6 +209,7 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by) 
   const T ux = (jx + T(0.5) * Fx) * inv_rho, uy = (jy + T(0.5) * Fy) * inv_rho;
   a.u[node] = ux;
   a.u[n + node] = uy;
+  if (RHO) rho_out[node] = rho;
   report_status(a.status, !finite_val(rho) || !(fabs(ux) <= a.u_cap) || !(fabs(uy) <= a.u_cap));
   const T uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
   const T om = a.omega, keep = T(1) - a.omega;

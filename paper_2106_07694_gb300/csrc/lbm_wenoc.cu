@@ -168,9 +168,13 @@ Args<T> make_args(const lbm_wenoc* h) {
 }
 
 // Kernel families for timing.
-enum Kind { K_LBM = 0, K_STAGE1, K_STAGE2, K_STAGE3, K_DEPOSIT, K_RK3_SWEEP, K_OTHER, K_COUNT };
-const char* kKindNames[K_COUNT] = {"lbm_collide_stream", "rk_stage1", "rk_stage2", "rk_stage3",
-                                   "deposit_reduce", "rk3_sweep2d", "other"};
+enum Kind {
+  K_LBM = 0, K_STAGE1, K_STAGE2, K_STAGE3, K_DEPOSIT, K_RK3_SWEEP, K_OTHER,
+  K_ADJ_FACES, K_ADJ_GATHER, K_ADJ_FLUID, K_COUNT
+};
+const char* kKindNames[K_COUNT] = {"lbm_collide_stream", "rk_stage1",  "rk_stage2",  "rk_stage3",
+                                   "deposit_reduce",     "rk3_sweep2d", "other",     "adj_faces",
+                                   "adj_gather",         "adj_gather_fluid"};
 // The 3D FP32 stage kernels are timed under the rk_stage* names.
 
 cudaEvent_t take_event(lbm_wenoc* h) {
@@ -219,6 +223,9 @@ void launch(lbm_wenoc* h, int kind, F&& f) {
 }
 
 template <class LAT, typename T>
+void enqueue_transport(lbm_wenoc* h, const Args<T>& a);
+
+template <class LAT, typename T>
 void enqueue_step(lbm_wenoc* h, int parity) {
   Args<T> a = make_args<T>(h);
   const dim3 blk(kLbmThreads);
@@ -239,6 +246,15 @@ void enqueue_step(lbm_wenoc* h, int parity) {
       }
     });
   }
+  enqueue_transport<LAT, T>(h, a);
+}
+
+// The three RK stages (and the deposit) of one step on the fields a points at.
+template <class LAT, typename T>
+void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
+  const dim3 blk(kLbmThreads);
+  const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
+  cudaStream_t s = h->stream;
   const long long nfloor = (long long)a.nx * (LAT::DIM == 3 ? a.ny : 1);
   const int dep_blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (nfloor + 4095) / 4096);
   if (std::is_same<T, float>::value && LAT::DIM == 2 && h->sweep) {
@@ -931,11 +947,11 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
 // ------------------------------------------------------------------------------------
 // Gradient of the deposited mass by checkpoint-and-recompute and the adjoint kernels.
 //
-// Adjoint workspace: a checkpoint (populations + c, the handle's layout from g to c) at
-// the start of every segment; one segment of step records (the handle's layout from g to
-// u: populations and c before the step, c1, c2 and u of the step); lambda of the
-// populations (two buffers, natural layout); mu, lc2, lc1, lc, lambda(u); lambda(Vs) and
-// its per-CTA partials; the face derivative records of one stage (24 fields).
+// Adjoint workspace: a checkpoint (populations + c, the handle's layout from g to c) at the
+// start of every segment but the last; one segment of step records (c before the step,
+// then the step's c1, c2, u and rho, which the recording steps write there directly);
+// lambda of the populations (two buffers, natural layout); mu, lc2, lc1, lc, lambda(u);
+// lambda(Vs) and its per-CTA partials; the face derivative records of one stage.
 
 namespace {
 
@@ -945,8 +961,8 @@ bool gradient_params_ok(const lbm_wenoc* h) {
 
 struct GradLayout {
   size_t ckpt, rec, lg0, lg1, mu, lc2, lc1, lc, lu, vs, vs_part, faces, total;
-  int nparts;  // per-CTA dJ/dVs partials of the face kernel
-  size_t ckpt_bytes, rec_bytes;  // one checkpoint, one step record
+  size_t ckpt_bytes, field_bytes, rec_bytes;  // one checkpoint, one field, one step record
+  int nparts;                                 // per-CTA dJ/dVs partials of the face kernel
   int64_t nseg;
 };
 
@@ -957,7 +973,8 @@ GradLayout grad_layout(const lbm_wenoc_params& p, int64_t nsteps, int32_t segmen
   GradLayout G{};
   G.nseg = (nsteps + segment - 1) / segment;
   G.ckpt_bytes = align_up(L.c + n * es - L.g, 256);
-  G.rec_bytes = align_up(L.u + 2 * n * es - L.g, 256);
+  G.field_bytes = align_up(n * es, 256);
+  G.rec_bytes = 6 * G.field_bytes;  // c, c1, c2, u (2), rho
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -985,32 +1002,66 @@ int copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
-// Reverse step over the step record `rec` (populations with parity par): mu = lambda(c^{n+1})
-// in, lambda(c^n) out; lam_next / lam_out = lambda of the populations of steps n+1 / n.
 template <typename T>
-int adjoint_step(lbm_wenoc* h, int par, const unsigned char* rec, const lw::AdjFields<T>& f,
-                 const lw::FaceRecords<T>& fr, const T* lam_next, T* lam_out) {
+struct StepRecord {
+  T *c, *c1, *c2, *u, *rho;
+};
+
+template <typename T>
+StepRecord<T> step_record(unsigned char* aw, const GradLayout& G, int64_t k) {
+  unsigned char* r = aw + G.rec + (size_t)k * G.rec_bytes;
+  StepRecord<T> R;
+  R.c = reinterpret_cast<T*>(r);
+  R.c1 = reinterpret_cast<T*>(r + G.field_bytes);
+  R.c2 = reinterpret_cast<T*>(r + 2 * G.field_bytes);
+  R.u = reinterpret_cast<T*>(r + 3 * G.field_bytes);  // u[d*n + node], d = 0, 1
+  R.rho = reinterpret_cast<T*>(r + 5 * G.field_bytes);
+  return R;
+}
+
+// One forward step that records what its adjoint needs: c^n is copied into the record,
+// and the step writes c1, c2, u and rho there instead of the handle's buffers.
+template <typename T>
+int record_step(lbm_wenoc* h, const StepRecord<T>& R) {
+  cudaStream_t s = h->stream;
+  const size_t n = (size_t)h->n;
+  if (copy_d2d(R.c, h->ws + h->L.c, n * sizeof(T), s) != LW_OK) return LW_ECUDA;
   Args<T> a = make_args<T>(h);
-  const Layout& L = h->L;
-  unsigned char* r = const_cast<unsigned char*>(rec);
-  a.g = reinterpret_cast<T*>(r);
-  a.c = reinterpret_cast<T*>(r + (L.c - L.g));
-  a.c1 = reinterpret_cast<T*>(r + (L.c1 - L.g));
-  a.c2 = reinterpret_cast<T*>(r + (L.c2 - L.g));
-  a.u = reinterpret_cast<T*>(r + (L.u - L.g));
+  a.c1 = R.c1;
+  a.c2 = R.c2;
+  a.u = R.u;
+  const dim3 blk(kLbmThreads), grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, 1);
+  launch(h, K_LBM, [&] {
+    if (h->parity == 0)
+      lw::lbm_d2q9_record_kernel<T, 0><<<grd, blk, 0, s>>>(a, R.rho);
+    else
+      lw::lbm_d2q9_record_kernel<T, 1><<<grd, blk, 0, s>>>(a, R.rho);
+  });
+  enqueue_transport<D2Q9, T>(h, a);
+  h->parity ^= 1;
+  h->steps += 1;
+  return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+// Reverse step over record R: mu = lambda(c^{n+1}) in, lambda(c^n) out; lam_next /
+// lam_out = lambda of the populations of steps n+1 / n.
+template <typename T>
+int adjoint_step(lbm_wenoc* h, const StepRecord<T>& R, const lw::AdjFields<T>& f, const lw::FaceRecords<T>& fr,
+                 const T* lam_next, T* lam_out) {
+  Args<T> a = make_args<T>(h);
+  a.c = R.c;
+  a.c1 = R.c1;
+  a.c2 = R.c2;
+  a.u = R.u;
   cudaStream_t s = h->stream;
   const dim3 blk(kLbmThreads), grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, 1);
-  lw::adj_faces_kernel<T, 3><<<grd, blk, 0, s>>>(a, f, fr);
-  lw::adj_gather_kernel<T, 3><<<grd, blk, 0, s>>>(a, f, fr);
-  lw::adj_faces_kernel<T, 2><<<grd, blk, 0, s>>>(a, f, fr);
-  lw::adj_gather_kernel<T, 2><<<grd, blk, 0, s>>>(a, f, fr);
-  lw::adj_faces_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, fr);
-  lw::adj_gather_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, fr);
-  if (par == 0)
-    lw::adj_fluid_kernel<T, 0><<<grd, blk, 0, s>>>(a, f, lam_next, lam_out);
-  else
-    lw::adj_fluid_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, lam_next, lam_out);
-  h->launches += 7;
+  launch(h, K_ADJ_FACES, [&] { lw::adj_faces_kernel<T, 3><<<grd, blk, 0, s>>>(a, f, fr); });
+  launch(h, K_ADJ_GATHER, [&] { lw::adj_gather_kernel<T, 3><<<grd, blk, 0, s>>>(a, f, fr); });
+  launch(h, K_ADJ_FACES, [&] { lw::adj_faces_kernel<T, 2><<<grd, blk, 0, s>>>(a, f, fr); });
+  launch(h, K_ADJ_GATHER, [&] { lw::adj_gather_kernel<T, 2><<<grd, blk, 0, s>>>(a, f, fr); });
+  launch(h, K_ADJ_FACES, [&] { lw::adj_faces_kernel<T, 1><<<grd, blk, 0, s>>>(a, f, fr); });
+  launch(h, K_ADJ_FLUID,
+         [&] { lw::adj_gather_fluid_kernel<T><<<grd, blk, 0, s>>>(a, f, fr, R.rho, lam_next, lam_out); });
   return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
@@ -1023,16 +1074,9 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   const Layout& L = h->L;
   unsigned char* state = h->ws + L.g;
   const size_t n = (size_t)h->n;
-  std::vector<int> rec_parity((size_t)segment);
-  // run the steps of one segment, recording each (populations and c before the step, then
-  // the step's c1, c2 and u)
   auto record_segment = [&](int64_t len) -> int {
     for (int64_t k = 0; k < len; ++k) {
-      unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
-      rec_parity[(size_t)k] = h->parity;
-      int r = copy_d2d(rec, state, G.ckpt_bytes, s);
-      if (r == LW_OK) r = lbm_wenoc_step(h, 1);
-      if (r == LW_OK) r = copy_d2d(rec + (L.c1 - L.g), h->ws + L.c1, L.u + 2 * n * sizeof(T) - L.c1, s);
+      const int r = record_step<T>(h, step_record<T>(aw, G, k));
       if (r != LW_OK) return r;
     }
     return LW_OK;
@@ -1068,27 +1112,26 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   fr.dwy = fr.dcx + 18 * n;
   T* lg[2] = {reinterpret_cast<T*>(aw + G.lg0), reinterpret_cast<T*>(aw + G.lg1)};
   if (cudaMemsetAsync(lg[0], 0, 9 * n * sizeof(T), s) != cudaSuccess) return LW_ECUDA;
-  lw::adj_init_kernel<T><<<(unsigned)((std::max<size_t>(n, (size_t)nparts) + 255) / 256), 256, 0, s>>>(
-      f, (long long)n, nparts);
-  h->launches += 1;
+  launch(h, K_OTHER, [&] {
+    lw::adj_init_kernel<T><<<(unsigned)((std::max<size_t>(n, (size_t)nparts) + 255) / 256), 256, 0, s>>>(
+        f, (long long)n, nparts);
+  });
   int cur = 0;
   for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
     const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
-    if (sg != G.nseg - 1) {  // recompute the segment from its checkpoint
+    if (sg != G.nseg - 1) {  // recompute the segment from its checkpoint, recording it
       if ((rc = copy_d2d(state, aw + G.ckpt + (size_t)sg * G.ckpt_bytes, G.ckpt_bytes, s)) != LW_OK) return rc;
       h->parity = ck_parity[(size_t)sg];
       h->cur = 0;
       if ((rc = record_segment(len)) != LW_OK) return rc;
     }
     for (int64_t k = len - 1; k >= 0; --k) {
-      const unsigned char* rec = aw + G.rec + (size_t)k * G.rec_bytes;
-      if ((rc = adjoint_step<T>(h, rec_parity[(size_t)k], rec, f, fr, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
+      if ((rc = adjoint_step<T>(h, step_record<T>(aw, G, k), f, fr, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
       cur ^= 1;
     }
   }
   // mu now holds lambda(c^0)
-  lw::adj_vs_finish_kernel<<<1, 256, 0, s>>>(f.vs_part, nparts, f.lam_vs);
-  h->launches += 1;
+  launch(h, K_OTHER, [&] { lw::adj_vs_finish_kernel<<<1, 256, 0, s>>>(f.vs_part, nparts, f.lam_vs); });
   cudaMemcpyKind k = is_device_pointer(grad_c0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (cudaMemcpyAsync(grad_c0, f.mu, n * sizeof(T), k, s) != cudaSuccess) return LW_ECUDA;
   if (cudaMemcpyAsync(dJ_dVs, f.lam_vs, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LW_ECUDA;

@@ -204,11 +204,13 @@ __global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2d
 inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
   if (override_rows > 0) return min(override_rows, ny);
   const long long strips = (nx + kS2T - 1) / kS2T;
-  // many short segments balance best (measured on the 2048 x 4096 lattice: 16 rows);
-  // fewer, longer ones when the lattice is small
-  long long segs = (27LL * sm_count + strips - 1) / strips;
-  int H = (int)((ny + segs - 1) / segs);
-  return max(min(16, ny), H);
+  // the longest segment (fewest priming rows) that still gives about 8.5 CTAs per SM;
+  // measured best: 16 rows on 2048 x 4096 and 1024 x 2048, 3-4 on 512 x 1024, 2 on 256 x 512
+  const int cand[] = {16, 12, 8, 6, 4, 3, 2};
+  for (int H : cand) {
+    if (strips * ((ny + H - 1) / H) >= 17LL * sm_count / 2) return min(H, ny);
+  }
+  return min(2, ny);
 }
 
 template <int STAGE>
