@@ -5,7 +5,8 @@ CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA library (``paper_2106_07694_gb300``) and never imports it.
 
 The arithmetic lives in ``lbm_wenoc_oracle.c`` (one routine per step a1..a9 of
-the method; see its header for the passages each follows).  This module only
+the method; see its header for the passages each follows; its last section is
+the reverse sweep for the gradient of the deposited mass).  This module only
 marshals numpy arrays.
 """
 import ctypes
@@ -68,6 +69,8 @@ def lib():
         L.orc_weno5_left.restype = ctypes.c_double
         L.orc_lattice.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), dp]
         L.orc_lattice.restype = ctypes.c_int
+        L.orc_deposit_gradient.argtypes = [ctypes.POINTER(_Params), dp, ctypes.c_int64, dp, dp, dp]
+        L.orc_deposit_gradient.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -83,6 +86,38 @@ def weno5_left(v, eps):
     return lib().orc_weno5_left(_dptr(v), float(eps))
 
 
+def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0, diffusivity=0.0,
+            lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False):
+    p = _Params()
+    p.dim = len(shape)
+    p.nx, p.ny = int(shape[0]), int(shape[1])
+    p.nz = int(shape[2]) if p.dim == 3 else 1
+    p.tau, p.gravity, p.density_contrast = tau, gravity, density_contrast
+    p.settling_velocity, p.diffusivity = settling_velocity, diffusivity
+    p.lf_alpha, p.u_cap = lf_alpha, u_cap
+    for d in range(3):
+        p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
+    p.flags = (ORC_PERIODIC_VERTICAL if periodic_vertical else 0) | \
+              (ORC_FROZEN_VELOCITY if frozen_velocity else 0)
+    return p
+
+
+def deposit_gradient(shape, c0, nsteps, **params):
+    """Reverse sweep of the oracle: (J, dJ/dc0, dJ/dVs) for the deposited mass after
+    nsteps steps from c0 (2D, walls, lf_alpha > 0 held fixed)."""
+    p = _params(shape, **params)
+    grid = (int(shape[1]), int(shape[0]))
+    c0 = np.ascontiguousarray(c0, dtype=np.float64).reshape(grid)
+    g = np.empty(grid)
+    dvs = ctypes.c_double()
+    J = ctypes.c_double()
+    rc = lib().orc_deposit_gradient(ctypes.byref(p), _dptr(c0), int(nsteps), _dptr(g), ctypes.byref(dvs),
+                                    ctypes.byref(J))
+    if rc != 0:
+        raise ValueError(f"orc_deposit_gradient failed: {rc}")
+    return J.value, g, dvs.value
+
+
 class OracleSim:
     """A simulation held by the C oracle.
 
@@ -94,17 +129,8 @@ class OracleSim:
                  settling_velocity=0.0, diffusivity=0.0, lf_alpha=0.0, u_cap=0.0,
                  body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False):
         dim = len(shape)
-        p = _Params()
-        p.dim = dim
-        p.nx, p.ny = int(shape[0]), int(shape[1])
-        p.nz = int(shape[2]) if dim == 3 else 1
-        p.tau, p.gravity, p.density_contrast = tau, gravity, density_contrast
-        p.settling_velocity, p.diffusivity = settling_velocity, diffusivity
-        p.lf_alpha, p.u_cap = lf_alpha, u_cap
-        for d in range(3):
-            p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
-        p.flags = (ORC_PERIODIC_VERTICAL if periodic_vertical else 0) | \
-                  (ORC_FROZEN_VELOCITY if frozen_velocity else 0)
+        p = _params(shape, tau, gravity, density_contrast, settling_velocity, diffusivity, lf_alpha, u_cap,
+                    body_force, periodic_vertical, frozen_velocity)
         self._p = p
         self.dim = dim
         self.grid = tuple(reversed([int(s) for s in shape]))  # numpy shape, vertical first

@@ -517,3 +517,297 @@ int orc_lattice(const orc_sim *s, int *ci, double *wi) {
   }
   return s->Q;
 }
+
+/* =====================================================================================
+ * Reverse sweep: gradient of the deposited mass (Sec. 4, m_b) after nsteps steps with
+ * respect to the initial concentration c0 and the settling velocity Vs (2D, walls, the
+ * Lax-Friedrichs alpha held fixed).
+ *
+ * The forward run keeps every step's state (populations and c before the step, the
+ * step's u, c1 and c2).  The reverse run then applies, step by step from the last, the
+ * transpose of each forward operation to the adjoint fields.  The local Jacobians are
+ * not derived by hand: each is the complex-step derivative  dF/dx = Im F(x + i h) / h
+ * (h = 1e-30, exact to rounding for the rational functions used here) of a complex twin
+ * of the forward routine above -- the WENO5 reconstruction, the face flux and the
+ * per-node BGK-Guo collision -- which restates it operation for operation in complex
+ * arithmetic.  Streaming, the Shu-Osher combinations and the deposit are linear and are
+ * transposed directly.
+ * ===================================================================================== */
+#include <complex.h>
+
+typedef double complex cplx;
+static const double kCstep = 1e-30;
+
+static cplx weno5_left_cx(const cplx v[5], double eps) {
+  const cplx a = v[0], b = v[1], c = v[2], d = v[3], e = v[4];
+  cplx q[3], beta[3];
+  q[0] = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  q[1] = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  q[2] = (2.0 * c + 5.0 * d - e) / 6.0;
+  beta[0] = 13.0 / 12.0 * (a - 2.0 * b + c) * (a - 2.0 * b + c) +
+            0.25 * (a - 4.0 * b + 3.0 * c) * (a - 4.0 * b + 3.0 * c);
+  beta[1] = 13.0 / 12.0 * (b - 2.0 * c + d) * (b - 2.0 * c + d) + 0.25 * (b - d) * (b - d);
+  beta[2] = 13.0 / 12.0 * (c - 2.0 * d + e) * (c - 2.0 * d + e) +
+            0.25 * (3.0 * c - 4.0 * d + e) * (3.0 * c - 4.0 * d + e);
+  const double lin[3] = {0.1, 0.6, 0.3};
+  cplx wt[3], sum = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    wt[k] = lin[k] / ((eps + beta[k]) * (eps + beta[k]));
+    sum += wt[k];
+  }
+  cplx h = 0.0;
+  for (int k = 0; k < 3; ++k) h += wt[k] / sum * q[k];
+  return h;
+}
+
+/* Face flux from its six stencil values c[0..5] and face-normal velocities w[0..5]
+ * (positions i-2 .. i+3; ghosts already mirrored by the caller), as in face_flux. */
+static cplx face_flux_cx(const orc_sim *s, const cplx cv[6], const cplx w[6]) {
+  cplx hp[6], hm[6];
+  for (int m = 0; m < 6; ++m) {
+    hp[m] = 0.5 * (w[m] + s->alpha) * cv[m];
+    hm[m] = 0.5 * (w[m] - s->alpha) * cv[m];
+  }
+  const cplx fplus = weno5_left_cx(hp, s->eps);
+  const cplx mirror[5] = {hm[5], hm[4], hm[3], hm[2], hm[1]};
+  const cplx fminus = weno5_left_cx(mirror, s->eps);
+  const cplx fdiff = -s->p.diffusivity * (cv[3] - cv[2]);
+  return fplus + fminus + fdiff;
+}
+
+/* Stencil of the face on the + side of node xyz along d, as face_flux reads it: node
+ * indices, ghost flags, c and w = u_d (odd at a wall) - Vs (vertical). */
+static void face_stencil(const orc_sim *s, const double *c, const int xyz[3], int d, size_t idx[6], int ghost[6],
+                         double cv[6], double w[6]) {
+  const int va = s->vaxis;
+  const int walls = vertical_walls(s) && d == va;
+  for (int m = -2; m <= 3; ++m) {
+    int p[3] = {xyz[0], xyz[1], xyz[2]};
+    int g = 0;
+    if (walls)
+      p[d] = reflect_vertical(xyz[d] + m, s->n[d], &g);
+    else
+      p[d] = wrap(xyz[d] + m, s->n[d]);
+    const size_t k = node_index(s, p[0], p[1], p[2]);
+    double ud = s->u[(size_t)d * s->nn + k];
+    if (g) ud = -ud;
+    idx[m + 2] = k;
+    ghost[m + 2] = g;
+    cv[m + 2] = c[k];
+    w[m + 2] = ud - (d == va ? s->p.settling_velocity : 0.0);
+  }
+}
+
+/* Transpose of L(c; u) applied to lamL: lam_c += (dL/dc)^T lamL, lam_u += (dL/du)^T lamL,
+ * *lam_vs += (dL/dVs)^T lamL.  L_k = sum_d (F_{k-1/2} - F_{k+1/2}), so the face on the +
+ * side of k carries lamF = lamL[next] - lamL[k]; the floor face F = -Vs c_0 enters L_0. */
+static void rate_adjoint(orc_sim *s, const double *c, const double *lamL, double *lam_c, double *lam_u,
+                         double *lam_vs, double *dfc, double *dfw) {
+  const size_t nn = s->nn;
+  const int dim = s->p.dim, va = s->vaxis, walls = vertical_walls(s);
+  for (int d = 0; d < dim; ++d) {
+    /* derivatives of every face flux (parallel), then the scatter (serial, index order) */
+#pragma omp parallel for schedule(static)
+    for (long long kk = 0; kk < (long long)nn; ++kk) {
+      const size_t k = (size_t)kk;
+      int xyz[3];
+      node_coords(s, k, xyz);
+      if (d == va && walls && xyz[d] == s->n[d] - 1) continue; /* lid: no face */
+      size_t idx[6];
+      int ghost[6];
+      double cv[6], w[6];
+      face_stencil(s, c, xyz, d, idx, ghost, cv, w);
+      for (int j = 0; j < 6; ++j) {
+        cplx cc[6], ww[6];
+        for (int m = 0; m < 6; ++m) {
+          cc[m] = cv[m];
+          ww[m] = w[m];
+        }
+        cc[j] += I * kCstep;
+        dfc[6 * k + j] = cimag(face_flux_cx(s, cc, ww)) / kCstep;
+        cc[j] = cv[j];
+        ww[j] += I * kCstep;
+        dfw[6 * k + j] = cimag(face_flux_cx(s, cc, ww)) / kCstep;
+      }
+    }
+    for (size_t k = 0; k < nn; ++k) {
+      int xyz[3];
+      node_coords(s, k, xyz);
+      if (d == va && walls && xyz[d] == s->n[d] - 1) continue;
+      int q[3] = {xyz[0], xyz[1], xyz[2]};
+      q[d] = wrap(xyz[d] + 1, s->n[d]);
+      const double lamF = lamL[node_index(s, q[0], q[1], q[2])] - lamL[k];
+      size_t idx[6];
+      int ghost[6];
+      double cv[6], w[6];
+      face_stencil(s, c, xyz, d, idx, ghost, cv, w);
+      for (int j = 0; j < 6; ++j) {
+        lam_c[idx[j]] += lamF * dfc[6 * k + j];
+        lam_u[(size_t)d * nn + idx[j]] += lamF * (ghost[j] ? -dfw[6 * k + j] : dfw[6 * k + j]);
+        if (d == va) *lam_vs -= lamF * dfw[6 * k + j]; /* w = +-u - Vs */
+      }
+    }
+  }
+  if (walls) {
+    for (size_t k = 0; k < nn; ++k) {
+      int xyz[3];
+      node_coords(s, k, xyz);
+      if (xyz[va] != 0) continue;
+      lam_c[k] -= s->p.settling_velocity * lamL[k];
+      *lam_vs -= c[k] * lamL[k];
+    }
+  }
+}
+
+/* Complex twin of one node of collide_all: populations f and concentration c in,
+ * post-collision populations and the velocity out. */
+static void collide_node_cx(const orc_sim *s, const cplx *f, cplx cval, cplx *fpost, cplx u[3]) {
+  const int Q = s->Q;
+  const double tau = s->p.tau, cs2 = 1.0 / 3.0;
+  cplx F[3];
+  for (int d = 0; d < 3; ++d) F[d] = s->p.body_force[d];
+  F[s->vaxis] -= s->p.gravity * s->p.density_contrast * cval;
+  cplx rho = 0.0, mom[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < Q; ++i) {
+    rho += f[i];
+    for (int d = 0; d < 3; ++d) mom[d] += f[i] * s->ci[i][d];
+  }
+  for (int d = 0; d < 3; ++d) u[d] = (mom[d] + 0.5 * F[d]) / rho;
+  const cplx uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int i = 0; i < Q; ++i) {
+    const cplx cu = s->ci[i][0] * u[0] + s->ci[i][1] * u[1] + s->ci[i][2] * u[2];
+    const cplx feq = s->wi[i] * rho * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+    cplx src = 0.0;
+    for (int d = 0; d < 3; ++d) src += ((s->ci[i][d] - u[d]) / cs2 + cu * s->ci[i][d] / (cs2 * cs2)) * F[d];
+    src *= (1.0 - 1.0 / (2.0 * tau)) * s->wi[i];
+    fpost[i] = f[i] - (f[i] - feq) / tau + src;
+  }
+}
+
+/* Reverse of collide + stream at every node: lam_next = lambda of the populations after
+ * streaming, lam_u = lambda of the step's velocity; out: lambda of the populations
+ * before the step (lam_f) and the buoyancy's share of lambda(c) (added to lam_c). */
+static void fluid_adjoint(orc_sim *s, const double *f, const double *c, const double *lam_next,
+                          const double *lam_u, double *lam_f, double *lam_c) {
+  const int Q = s->Q, dim = s->p.dim, va = s->vaxis, walls = vertical_walls(s);
+  const size_t nn = s->nn;
+#pragma omp parallel for schedule(static)
+  for (long long kk = 0; kk < (long long)nn; ++kk) {
+    const size_t k = (size_t)kk;
+    int xyz[3];
+    node_coords(s, k, xyz);
+    /* adjoint of the post-collision populations: where streaming sent each one */
+    double lpost[19];
+    for (int i = 0; i < Q; ++i) {
+      int to[3];
+      int hits_wall = 0;
+      for (int d = 0; d < 3; ++d) {
+        to[d] = xyz[d] + s->ci[i][d];
+        if (d == va && walls && (to[d] < 0 || to[d] >= s->n[d]))
+          hits_wall = 1;
+        else
+          to[d] = wrap(to[d], s->n[d]);
+      }
+      lpost[i] = hits_wall ? lam_next[(size_t)s->opp[i] * nn + k]
+                           : lam_next[(size_t)i * nn + node_index(s, to[0], to[1], to[2])];
+    }
+    /* Jacobian columns of (fpost, u) with respect to each f_j and c, by complex step */
+    cplx fin[19], fpost[19], u[3];
+    for (int j = 0; j <= Q; ++j) {
+      for (int i = 0; i < Q; ++i) fin[i] = f[(size_t)i * nn + k];
+      cplx cval = c[k];
+      if (j < Q)
+        fin[j] += I * kCstep;
+      else
+        cval += I * kCstep;
+      collide_node_cx(s, fin, cval, fpost, u);
+      double acc = 0.0;
+      for (int i = 0; i < Q; ++i) acc += lpost[i] * cimag(fpost[i]) / kCstep;
+      for (int d = 0; d < dim; ++d) acc += lam_u[(size_t)d * nn + k] * cimag(u[d]) / kCstep;
+      if (j < Q)
+        lam_f[(size_t)j * nn + k] = acc;
+      else
+        lam_c[k] += acc;
+    }
+  }
+}
+
+/* J = deposited mass after nsteps steps from c0 (fluid at rest); grad_c0 = dJ/dc0,
+ * *dJ_dVs = dJ/dVs at fixed alpha.  2D with walls, lf_alpha > 0, velocity not frozen. */
+int orc_deposit_gradient(const orc_params *p, const double *c0, int64_t nsteps, double *grad_c0, double *dJ_dVs,
+                         double *J) {
+  if (!p || !c0 || !grad_c0 || !dJ_dVs || !J || nsteps < 1) return ORC_EINVAL;
+  if (p->dim != 2 || (p->flags & (ORC_PERIODIC_VERTICAL | ORC_FROZEN_VELOCITY)) || !(p->lf_alpha > 0.0))
+    return ORC_EINVAL;
+  orc_sim *s = orc_create(p);
+  if (!s) return ORC_EINVAL;
+  const int Q = s->Q, dim = s->p.dim;
+  const size_t nn = s->nn, per = (size_t)(Q + 3 + dim) * nn; /* f, c, c1, c2, u */
+  double *hist = (double *)malloc(per * (size_t)nsteps * sizeof(double));
+  double *work = (double *)calloc((size_t)(2 * Q + 5 + dim + 12) * nn, sizeof(double));
+  if (!hist || !work) {
+    free(hist);
+    free(work);
+    orc_destroy(s);
+    return ORC_ENOMEM;
+  }
+  orc_init(s, c0, NULL);
+  for (int64_t t = 0; t < nsteps; ++t) {
+    double *h = hist + per * (size_t)t;
+    memcpy(h, s->f, (size_t)Q * nn * sizeof(double));
+    memcpy(h + (size_t)Q * nn, s->c, nn * sizeof(double));
+    orc_step(s, 1);
+    memcpy(h + (size_t)(Q + 1) * nn, s->c1, nn * sizeof(double));
+    memcpy(h + (size_t)(Q + 2) * nn, s->c2, nn * sizeof(double));
+    memcpy(h + (size_t)(Q + 3) * nn, s->u, (size_t)dim * nn * sizeof(double));
+  }
+  *J = s->deposit;
+  double *lam_next = work, *lam_f = work + (size_t)Q * nn;
+  double *mu = work + (size_t)2 * Q * nn, *lc2 = mu + nn, *lc1 = lc2 + nn, *lc = lc1 + nn, *lamL = lc + nn;
+  double *lam_u = lamL + nn, *dfc = lam_u + (size_t)dim * nn, *dfw = dfc + 6 * nn;
+  double lam_vs = 0.0;
+  const double vs = s->p.settling_velocity;
+  /* lambda(c^N) = 0 and lambda(f^N) = 0: J does not depend on the final state */
+  for (int64_t t = nsteps - 1; t >= 0; --t) {
+    const double *h = hist + per * (size_t)t;
+    const double *f = h, *c = h + (size_t)Q * nn, *c1 = h + (size_t)(Q + 1) * nn, *c2 = h + (size_t)(Q + 2) * nn;
+    memcpy(s->u, h + (size_t)(Q + 3) * nn, (size_t)dim * nn * sizeof(double));
+    for (size_t k = 0; k < (size_t)dim * nn; ++k) lam_u[k] = 0.0;
+    /* deposit += Vs (sum_floor c/6 + c1/6 + 2 c2/3) */
+    for (int x = 0; x < s->n[0]; ++x) {
+      const size_t k = node_index(s, x, 0, 0);
+      lam_vs += c[k] / 6.0 + c1[k] / 6.0 + 2.0 * c2[k] / 3.0;
+    }
+    /* stage 3: c' = c/3 + 2 c2/3 + 2 L(c2)/3 */
+    for (size_t k = 0; k < nn; ++k) {
+      lamL[k] = 2.0 * mu[k] / 3.0;
+      lc2[k] = 2.0 * mu[k] / 3.0;
+    }
+    for (int x = 0; x < s->n[0]; ++x) lc2[node_index(s, x, 0, 0)] += 2.0 * vs / 3.0;
+    rate_adjoint(s, c2, lamL, lc2, lam_u, &lam_vs, dfc, dfw);
+    /* stage 2: c2 = 3c/4 + c1/4 + L(c1)/4 */
+    for (size_t k = 0; k < nn; ++k) {
+      lamL[k] = 0.25 * lc2[k];
+      lc1[k] = 0.25 * lc2[k];
+    }
+    for (int x = 0; x < s->n[0]; ++x) lc1[node_index(s, x, 0, 0)] += vs / 6.0;
+    rate_adjoint(s, c1, lamL, lc1, lam_u, &lam_vs, dfc, dfw);
+    /* stage 1: c1 = c + L(c) */
+    for (size_t k = 0; k < nn; ++k) {
+      lamL[k] = lc1[k];
+      lc[k] = mu[k] / 3.0 + 0.75 * lc2[k] + lc1[k];
+    }
+    for (int x = 0; x < s->n[0]; ++x) lc[node_index(s, x, 0, 0)] += vs / 6.0;
+    rate_adjoint(s, c, lamL, lc, lam_u, &lam_vs, dfc, dfw);
+    /* fluid step */
+    fluid_adjoint(s, f, c, lam_next, lam_u, lam_f, lc);
+    memcpy(lam_next, lam_f, (size_t)Q * nn * sizeof(double));
+    memcpy(mu, lc, nn * sizeof(double));
+  }
+  memcpy(grad_c0, mu, nn * sizeof(double));
+  *dJ_dVs = lam_vs;
+  free(hist);
+  free(work);
+  orc_destroy(s);
+  return ORC_OK;
+}

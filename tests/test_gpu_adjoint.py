@@ -1,5 +1,6 @@
 """Gradient of the deposited mass (Sec. 4, m_b) by the hand-written adjoint of the 2D
-coupled step, checked against central finite differences of the FP64 oracle.
+coupled step, checked against central finite differences of the FP64 oracle and against
+the oracle's own reverse sweep.
 
 J(c0, Vs) = mass through the floor after N steps from c0 with the fluid at rest.  The
 adjoint (reverse sweep with checkpoint-and-recompute) is exact up to rounding, so:
@@ -7,6 +8,8 @@ adjoint (reverse sweep with checkpoint-and-recompute) is exact up to rounding, s
     difference (h = 1e-6) to 1e-6 of the largest component, relative L2 <= 1e-7;
   * FP64, a lattice spanning two 128-column blocks with a ragged tail and a ragged last
     segment: directional derivative and dJ/dVs (lf_alpha held fixed) to 1e-7;
+  * 64 x 128, 100 steps: element by element against the oracle's reverse sweep, FP64 to
+    1e-10, FP32 to 1e-3;
   * FP32 against the FP64 adjoint: relative L2 <= 1e-3;
   * the checkpoint spacing does not change the result (bitwise, FP64 and FP32); autograd
     wraps the same numbers.
@@ -83,6 +86,25 @@ def test_adjoint_every_component_vs_oracle_fd():
     assert np.abs(fd - fd0).flat[::7].max() > 1e-3 * scale
     assert np.abs(g - fd).max() <= 1e-6 * scale
     assert rel_l2(g, fd) <= 1e-7
+
+
+def test_adjoint_vs_oracle_reverse_sweep_64x128():
+    # the oracle's own reverse sweep (complex-step Jacobians of its forward routines),
+    # element by element: FP64 to rounding, FP32 to its precision
+    shape, nsteps = (64, 128), 100
+    c0 = _c0(shape, 21)
+    Jo, go, vo = oracle.deposit_gradient(shape, c0, nsteps, **ADJ)
+    J, g, dvs = _gpu_grad(shape, c0, nsteps, segment=30, **ADJ)
+    assert J == pytest.approx(Jo, rel=1e-12)
+    assert rel_l2(g, go) <= 1e-10
+    assert np.abs(g - go).max() <= 1e-10 * np.abs(go).max()
+    assert dvs == pytest.approx(vo, rel=1e-10)
+    c32 = c0.astype(np.float32).astype(np.float64)
+    Jo32, go32, vo32 = oracle.deposit_gradient(shape, c32, nsteps, **ADJ)
+    J, g, dvs = _gpu_grad(shape, c32, nsteps, segment=30, fp64=False, **ADJ)
+    assert J == pytest.approx(Jo32, rel=1e-5)
+    assert rel_l2(g, go32) <= 1e-3
+    assert dvs == pytest.approx(vo32, rel=1e-3)
 
 
 def test_adjoint_directional_and_vs_ragged():
@@ -183,10 +205,12 @@ def test_adjoint_rejects_unsupported_and_restores_state():
 
 
 # ---- the 512 x 1024 FP32 gradient over 2000 steps (state kept every 100) -------------
-# Expected values: central differences of the FP64 forward (h = 1e-6 along a direction,
-# 1e-7 in Vs; WENO5's eps = 1e-6 makes J strongly nonlinear for c near 0, so h must stay
-# well below 1e-5).  Measured: FP32 adjoint against these within 5e-7 of sum|g d|, the
-# FD truncation near 1e-8 of it; dJ/dVs within 4e-7 relative.
+# Expected values: central differences of the FP64 forward along random unit directions
+# d (seed 1), J(c0 + 1e-3 d) - J(c0 - 1e-3 d) over 2e-3, i.e. about 1.4e-6 per node
+# (WENO5's eps = 1e-6 makes J strongly nonlinear for c near 0: a per-node step of 1e-5
+# already leaves a 1e-3 relative truncation error), and in Vs with step 1e-7.  Bound: 1e-4
+# relative, with a floor of 1e-6 sum|g d| for directions whose derivative nearly cancels.
+# Measured: FP32 adjoint within 3e-5 relative of these, dJ/dVs within 4e-7.
 
 def _full_fd_check(n_dirs):
     from paper_2106_07694_gb300 import lbm_wenoc as lw
@@ -207,13 +231,14 @@ def _full_fd_check(n_dirs):
         return sim.deposit
 
     assert J == pytest.approx(J64(c0), rel=1e-5, abs=1e-9)
-    rng = np.random.default_rng(2106)
-    h = 1e-6
+    rng = np.random.default_rng(1)
+    h = 1e-3
     for _ in range(n_dirs):
         d = rng.standard_normal(c0.shape)
+        d /= np.linalg.norm(d)
         fd = (J64(c0 + h * d) - J64(c0 - h * d)) / (2 * h)
-        scale = float(np.sum(np.abs(g * d)))
-        assert abs(float(np.sum(g * d)) - fd) <= 5e-6 * scale, (fd, float(np.sum(g * d)), scale)
+        got = float(np.sum(g * d))
+        assert abs(got - fd) <= 1e-4 * abs(fd) + 1e-6 * float(np.sum(np.abs(g * d))), (got, fd)
     hv = 1e-7
     sp = lw.Simulation(wl.shape, fp64=True, settling_velocity=vs + hv, **kw)
     sm = lw.Simulation(wl.shape, fp64=True, settling_velocity=vs - hv, **kw)
