@@ -122,10 +122,12 @@ class ClockSampler:
 # taken on; a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
     "rk3_sweep2d": (127.72e6, "paper_2106_07694_gb300/csrc/transport_sweep2d.cuh", "83e0464e30c5"),
-    "lbm_collide_stream": (645.79e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "3777e2a15a91"),
-    "rk_stage1": (116.03e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "d79897d5bdd3"),
-    "rk_stage2": (154.79e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "d79897d5bdd3"),
-    "rk_stage3": (149.83e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "d79897d5bdd3"),
+    "lbm_collide_stream": (644.06e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "fa3b480929ff"),
+    "rk_stage1": (112.81e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "61f5d8230dc8"),
+    "rk_stage2": (151.05e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "61f5d8230dc8"),
+    "rk_stage3": (146.58e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "61f5d8230dc8"),
+    # 512 x 1024 adjoint workload (the face records stay in L2)
+    "adj_faces": (9.12e6, "paper_2106_07694_gb300/csrc/adjoint.cuh", "bb59bd120597"),
 }
 
 
@@ -527,7 +529,8 @@ def bench_adjoint(args):
             "kernel": "adj_faces", "bound": "alu", "alg_flop_per_node": ADJ_FACES_FLOP,
             "achieved": ADJ_FACES_FLOP * nodes / (faces_us * 1e-6) / 1e12, "peak": peak_alu,
             "unit": "TFLOP/s", "frac": ADJ_FACES_FLOP * nodes / (faces_us * 1e-6) / 1e12 / peak_alu,
-            "traffic": None},
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sampled SM clock",
+            "traffic": kernel_traffic("adj_faces")},
         "e2e": {"value": nodes * nsteps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * nodes / nsteps,
                 "d2h_bytes_per_step": (4 * nodes + 8) / nsteps},
         "gpu_launches": int(launches), "clocks": clk,
