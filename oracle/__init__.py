@@ -18,6 +18,7 @@ from . import build as _build
 
 ORC_PERIODIC_VERTICAL = 1
 ORC_FROZEN_VELOCITY = 2
+ORC_SUGAR = 4
 
 
 class _Params(ctypes.Structure):
@@ -35,6 +36,10 @@ class _Params(ctypes.Structure):
         ("u_cap", ctypes.c_double),
         ("body_force", ctypes.c_double * 3),
         ("flags", ctypes.c_uint32),
+        ("sugar_contrast", ctypes.c_double),
+        ("sugar_diffusivity", ctypes.c_double),
+        ("phi0", ctypes.c_double),
+        ("vs_sugar", ctypes.c_double),
     ]
 
 
@@ -71,6 +76,9 @@ def lib():
         L.orc_lattice.restype = ctypes.c_int
         L.orc_deposit_gradient.argtypes = [ctypes.POINTER(_Params), dp, ctypes.c_int64, dp, dp, dp]
         L.orc_deposit_gradient.restype = ctypes.c_int
+        L.orc_set_sugar.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_sugar.restype = ctypes.c_int
+        L.orc_sugar.argtypes = [ctypes.c_void_p, dp]
         _lib = L
     return _lib
 
@@ -87,7 +95,8 @@ def weno5_left(v, eps):
 
 
 def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0, diffusivity=0.0,
-            lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False):
+            lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False,
+            sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0):
     p = _Params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -98,7 +107,8 @@ def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity
     for d in range(3):
         p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
     p.flags = (ORC_PERIODIC_VERTICAL if periodic_vertical else 0) | \
-              (ORC_FROZEN_VELOCITY if frozen_velocity else 0)
+              (ORC_FROZEN_VELOCITY if frozen_velocity else 0) | (ORC_SUGAR if sugar else 0)
+    p.sugar_contrast, p.sugar_diffusivity, p.phi0, p.vs_sugar = sugar_contrast, sugar_diffusivity, phi0, vs_sugar
     return p
 
 
@@ -127,10 +137,12 @@ class OracleSim:
 
     def __init__(self, shape, tau=0.6, gravity=0.0, density_contrast=1.0,
                  settling_velocity=0.0, diffusivity=0.0, lf_alpha=0.0, u_cap=0.0,
-                 body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False):
+                 body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False,
+                 sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0):
         dim = len(shape)
         p = _params(shape, tau, gravity, density_contrast, settling_velocity, diffusivity, lf_alpha, u_cap,
-                    body_force, periodic_vertical, frozen_velocity)
+                    body_force, periodic_vertical, frozen_velocity, sugar, sugar_contrast, sugar_diffusivity,
+                    phi0, vs_sugar)
         self._p = p
         self.dim = dim
         self.grid = tuple(reversed([int(s) for s in shape]))  # numpy shape, vertical first
@@ -161,6 +173,18 @@ class OracleSim:
         rc = lib().orc_init(self._h, _dptr(c0), up)
         if rc != 0:
             raise RuntimeError(f"orc_init failed: {rc}")
+
+    def set_sugar(self, S0):
+        """Sugar field (sugar=True handles), after init."""
+        S0 = np.ascontiguousarray(S0, dtype=np.float64).reshape(self.grid)
+        self._S_keep = S0
+        if lib().orc_set_sugar(self._h, _dptr(S0)) != 0:
+            raise RuntimeError("orc_set_sugar failed")
+
+    def sugar(self):
+        S = np.empty(self.grid)
+        lib().orc_sugar(self._h, _dptr(S))
+        return S
 
     def step(self, n=1):
         return lib().orc_step(self._h, int(n))

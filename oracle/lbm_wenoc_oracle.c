@@ -20,6 +20,13 @@
  *   a8  SSP-RK3 (Shu-Osher) with the velocity frozen at step n     (Supplement Eqs. S21-S23)
  *   a9  deposit: settling flux through the floor, RK3 b-weights    (Sec. 4, deposited mass m_b)
  *
+ * With ORC_SUGAR, a second scalar S (sugar, normalised by its lower-layer value S0):
+ *   s1  force F_v = -g [R c + S* S (1 - phi0 c)]                   (Eq. forceterm; rho/rho0 - 1 = S* S)
+ *   s2  settling velocity Vs (1 - kS S) in every face velocity     (Eq. stokes_vel with rho(S))
+ *   s3  S advanced by first-order upwind in advective form, one    (Eq. AD; Supplement Eqs. S5, S6)
+ *       explicit step per axis sign, plus central diffusion D_s,
+ *       with the velocity of a1 and Neumann walls (Eq. neum2)
+ *
  * Readings of points the paper leaves open (garbled LBE right-hand side,
  * WENO order, split, epsilon, wall fluxes, coupling order, initial state) are
  * the ones listed in the design notes: fluid nodes sit at v = 0..N-1 on the
@@ -38,6 +45,7 @@
 
 #define ORC_PERIODIC_VERTICAL 1u /* vertical axis periodic too: no walls, no deposit */
 #define ORC_FROZEN_VELOCITY 2u   /* fluid not advanced; transport uses the velocity given at init */
+#define ORC_SUGAR 4u             /* second scalar S (sugar) in the force, Vs and its own transport */
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -56,6 +64,10 @@ typedef struct {
   double u_cap;    /* 0 selects 0.1 */
   double body_force[3];
   uint32_t flags;
+  double sugar_contrast;    /* S*: rho/rho0 - 1 at S = 1 */
+  double sugar_diffusivity; /* D_s */
+  double phi0;              /* particle volume fraction at c = 1, in the (1 - phi) factor */
+  double vs_sugar;          /* kS: Vs(S) = Vs (1 - kS S) */
 } orc_params;
 
 typedef struct {
@@ -75,6 +87,7 @@ typedef struct {
   double *u; /* dim*nn: velocity that transports c during the current step */
   double *rho;
   double *c1, *c2, *L, *flux;
+  double *S, *Snew; /* sugar (ORC_SUGAR) */
   double deposit;
   int64_t steps;
   int status;
@@ -140,11 +153,24 @@ static int wrap(int a, int n) {
 
 static int vertical_walls(const orc_sim *s) { return !(s->p.flags & ORC_PERIODIC_VERTICAL); }
 
+static int sugar_on(const orc_sim *s) { return (s->p.flags & ORC_SUGAR) != 0; }
+
 /* Buoyancy + external body force at a node: F = body - A c e_v, A = g (rho_p - rho_0)/rho_0
- * (Eq. forceterm with the sugar term dropped and phi read as c). */
-static void node_force(const orc_sim *s, double cval, double F[3]) {
+ * (Eq. forceterm with phi read as c); with sugar also - g S* S (1 - phi0 c) e_v (its
+ * second term, rho/rho0 - 1 = S* S). */
+static void node_force_s(const orc_sim *s, double cval, double sval, double F[3]) {
   for (int d = 0; d < 3; ++d) F[d] = s->p.body_force[d];
   F[s->vaxis] -= s->p.gravity * s->p.density_contrast * cval;
+  if (sugar_on(s)) F[s->vaxis] -= s->p.gravity * s->p.sugar_contrast * sval * (1.0 - s->p.phi0 * cval);
+}
+
+static void node_force(const orc_sim *s, size_t k, double F[3]) {
+  node_force_s(s, s->c[k], sugar_on(s) ? s->S[k] : 0.0, F);
+}
+
+/* Settling velocity at node k: Vs, or Vs (1 - kS S_k) with sugar. */
+static double settling_at(const orc_sim *s, size_t k) {
+  return sugar_on(s) ? s->p.settling_velocity * (1.0 - s->p.vs_sugar * s->S[k]) : s->p.settling_velocity;
 }
 
 /* ---- a1 + a2: moments and BGK-Guo collision at every node ---- */
@@ -157,7 +183,7 @@ static void collide_all(orc_sim *s) {
   for (long long kk = 0; kk < (long long)nn; ++kk) {
     size_t k = (size_t)kk;
     double F[3];
-    node_force(s, s->c[k], F);
+    node_force(s, k, F);
     double rho = 0.0, mom[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < Q; ++i) {
       double fi = s->f[(size_t)i * nn + k];
@@ -272,7 +298,7 @@ static double face_flux(const orc_sim *s, const double *c, int xyz[3], int d) {
     double cval = c[k];
     double ud = s->u[(size_t)d * nn + k];
     if (ghost) ud = -ud; /* no-slip wall: velocity odd about the wall */
-    double w = ud - (d == va ? s->p.settling_velocity : 0.0);
+    double w = ud - (d == va ? settling_at(s, k) : 0.0);
     cv[m + 2] = cval;
     hp[m + 2] = 0.5 * (w + s->alpha) * cval;
     hm[m + 2] = 0.5 * (w - s->alpha) * cval;
@@ -312,7 +338,7 @@ static void transport_rate(orc_sim *s, const double *c, double *L) {
       node_coords(s, k, xyz);
       double fminus;
       if (d == va && walls && xyz[d] == 0) {
-        fminus = -s->p.settling_velocity * c[k]; /* floor: settling outflow */
+        fminus = -settling_at(s, k) * c[k]; /* floor: settling outflow */
       } else {
         int p[3] = {xyz[0], xyz[1], xyz[2]};
         p[d] = wrap(xyz[d] - 1, s->n[d]);
@@ -335,6 +361,25 @@ static double floor_sum(const orc_sim *s, const double *c) {
   return acc;
 }
 
+/* With sugar: settling outflow through the floor, the sum of Vs(S) c over the floor
+ * row/plane, serial and in index order. */
+static double floor_outflow(const orc_sim *s, const double *c) {
+  double acc = 0.0;
+  if (s->p.dim == 2) {
+    for (int x = 0; x < s->n[0]; ++x) {
+      const size_t k = node_index(s, x, 0, 0);
+      acc += settling_at(s, k) * c[k];
+    }
+  } else {
+    for (int y = 0; y < s->n[1]; ++y)
+      for (int x = 0; x < s->n[0]; ++x) {
+        const size_t k = node_index(s, x, y, 0);
+        acc += settling_at(s, k) * c[k];
+      }
+  }
+  return acc;
+}
+
 /* ---- a8 + a9: SSP-RK3 (S21-S23) with dt = 1, velocity frozen, deposit by b-weights ---- */
 
 static void rk3_transport(orc_sim *s) {
@@ -345,12 +390,56 @@ static void rk3_transport(orc_sim *s) {
   transport_rate(s, c1, L);
   for (size_t k = 0; k < nn; ++k) c2[k] = 0.75 * c[k] + 0.25 * c1[k] + 0.25 * L[k];
   double dep = 0.0;
-  if (vertical_walls(s))
-    dep = s->p.settling_velocity *
-          (floor_sum(s, c) / 6.0 + floor_sum(s, c1) / 6.0 + 2.0 * floor_sum(s, c2) / 3.0);
+  if (vertical_walls(s)) {
+    if (sugar_on(s))
+      dep = floor_outflow(s, c) / 6.0 + floor_outflow(s, c1) / 6.0 + 2.0 * floor_outflow(s, c2) / 3.0;
+    else
+      dep = s->p.settling_velocity *
+            (floor_sum(s, c) / 6.0 + floor_sum(s, c1) / 6.0 + 2.0 * floor_sum(s, c2) / 3.0);
+  }
   transport_rate(s, c2, L);
   for (size_t k = 0; k < nn; ++k) c[k] = c[k] / 3.0 + 2.0 * c2[k] / 3.0 + 2.0 * L[k] / 3.0;
   s->deposit += dep;
+}
+
+/* ---- s3: sugar, first-order upwind (S5 for u > 0, S6 for u < 0) per axis, explicit, in
+ * the advective form the paper prints, plus central diffusion; Neumann walls read the
+ * mirror node (S_{-1} = S_0). ---- */
+static void sugar_transport(orc_sim *s) {
+  const size_t nn = s->nn;
+  const int dim = s->p.dim, va = s->vaxis, walls = vertical_walls(s);
+  const double Ds = s->p.sugar_diffusivity;
+#pragma omp parallel for schedule(static)
+  for (long long kk = 0; kk < (long long)nn; ++kk) {
+    const size_t k = (size_t)kk;
+    int xyz[3];
+    node_coords(s, k, xyz);
+    const double a = s->S[k];
+    double next = a;
+    for (int d = 0; d < dim; ++d) {
+      int pm[3] = {xyz[0], xyz[1], xyz[2]}, pp[3] = {xyz[0], xyz[1], xyz[2]};
+      if (d == va && walls) {
+        int g;
+        pm[d] = reflect_vertical(xyz[d] - 1, s->n[d], &g);
+        pp[d] = reflect_vertical(xyz[d] + 1, s->n[d], &g);
+      } else {
+        pm[d] = wrap(xyz[d] - 1, s->n[d]);
+        pp[d] = wrap(xyz[d] + 1, s->n[d]);
+      }
+      const double am = s->S[node_index(s, pm[0], pm[1], pm[2])];
+      const double ap = s->S[node_index(s, pp[0], pp[1], pp[2])];
+      const double u = s->u[(size_t)d * nn + k];
+      if (u > 0.0)
+        next -= u * (a - am); /* S5, dt = dx = 1 */
+      else
+        next -= u * (ap - a); /* S6 */
+      next += Ds * (ap - 2.0 * a + am);
+    }
+    s->Snew[k] = next;
+  }
+  double *t = s->S;
+  s->S = s->Snew;
+  s->Snew = t;
 }
 
 static void check_state(orc_sim *s) {
@@ -396,9 +485,12 @@ orc_sim *orc_create(const orc_params *p) {
   s->flux = (double *)calloc(nn, sizeof(double));
   s->rho = (double *)calloc(nn, sizeof(double));
   s->u = (double *)calloc((size_t)s->p.dim * nn, sizeof(double));
-  if (!s->f || !s->fpost || !s->c || !s->c1 || !s->c2 || !s->L || !s->flux || !s->rho || !s->u) {
+  s->S = (double *)calloc(nn, sizeof(double));
+  s->Snew = (double *)calloc(nn, sizeof(double));
+  if (!s->f || !s->fpost || !s->c || !s->c1 || !s->c2 || !s->L || !s->flux || !s->rho || !s->u || !s->S ||
+      !s->Snew) {
     free(s->f); free(s->fpost); free(s->c); free(s->c1); free(s->c2);
-    free(s->L); free(s->flux); free(s->rho); free(s->u); free(s);
+    free(s->L); free(s->flux); free(s->rho); free(s->u); free(s->S); free(s->Snew); free(s);
     return NULL;
   }
   return s;
@@ -407,7 +499,7 @@ orc_sim *orc_create(const orc_params *p) {
 void orc_destroy(orc_sim *s) {
   if (!s) return;
   free(s->f); free(s->fpost); free(s->c); free(s->c1); free(s->c2);
-  free(s->L); free(s->flux); free(s->rho); free(s->u);
+  free(s->L); free(s->flux); free(s->rho); free(s->u); free(s->S); free(s->Snew);
   free(s);
 }
 
@@ -431,11 +523,21 @@ int orc_init(orc_sim *s, const double *c0, const double *u0) {
     }
     s->rho[k] = 1.0;
   }
+  memset(s->S, 0, nn * sizeof(double));
   s->deposit = 0.0;
   s->steps = 0;
   s->status = ORC_OK;
   return ORC_OK;
 }
+
+/* Sugar field (ORC_SUGAR), set after orc_init and read back. */
+int orc_set_sugar(orc_sim *s, const double *S0) {
+  if (!s || !S0 || !sugar_on(s)) return ORC_EINVAL;
+  memcpy(s->S, S0, s->nn * sizeof(double));
+  return ORC_OK;
+}
+
+void orc_sugar(const orc_sim *s, double *S) { memcpy(S, s->S, s->nn * sizeof(double)); }
 
 /* One coupled step = a1..a3 on the populations (unless the velocity is frozen),
  * then a4..a9 on c with the velocity of a1 (O7: u at time n, frozen over the stages). */
@@ -447,6 +549,7 @@ int orc_step(orc_sim *s, int64_t nsteps) {
       stream_all(s);
     }
     rk3_transport(s);
+    if (sugar_on(s)) sugar_transport(s);
     check_state(s);
     s->steps++;
   }
@@ -465,7 +568,7 @@ void orc_fields(const orc_sim *s, double *rho, double *u, double *c) {
         for (int d = 0; d < s->p.dim; ++d) u[(size_t)d * nn + k] = s->u[(size_t)d * nn + k];
     } else {
       double F[3];
-      node_force(s, s->c[k], F);
+      node_force(s, k, F);
       double r = 0.0, mom[3] = {0.0, 0.0, 0.0};
       for (int i = 0; i < s->Q; ++i) {
         double fi = s->f[(size_t)i * nn + k];
@@ -737,7 +840,8 @@ static void fluid_adjoint(orc_sim *s, const double *f, const double *c, const do
 int orc_deposit_gradient(const orc_params *p, const double *c0, int64_t nsteps, double *grad_c0, double *dJ_dVs,
                          double *J) {
   if (!p || !c0 || !grad_c0 || !dJ_dVs || !J || nsteps < 1) return ORC_EINVAL;
-  if (p->dim != 2 || (p->flags & (ORC_PERIODIC_VERTICAL | ORC_FROZEN_VELOCITY)) || !(p->lf_alpha > 0.0))
+  if (p->dim != 2 || (p->flags & (ORC_PERIODIC_VERTICAL | ORC_FROZEN_VELOCITY | ORC_SUGAR)) ||
+      !(p->lf_alpha > 0.0))
     return ORC_EINVAL;
   orc_sim *s = orc_create(p);
   if (!s) return ORC_EINVAL;
