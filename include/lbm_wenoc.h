@@ -51,6 +51,10 @@ extern "C" {
 #define LW_NO_GRAPH 0x8u          /* launch kernels one by one instead of replaying CUDA graphs */
 #define LW_FUSED_RK3 0x10u        /* 2D FP32: the three RK stages in one fused sweep kernel instead of
                                      three row-sweep launches (same results to rounding) */
+#define LW_SUGAR 0x20u            /* second scalar S, the paper's sugar (Eqs. AD, forceterm, stokes_vel):
+                                     force -g S* S (1 - phi0 c), settling velocity Vs (1 - kS S), S
+                                     advected by first-order upwind (Supplement Eqs. S5, S6) with
+                                     diffusion D_s; not with LW_FUSED_RK3, batches or the gradient */
 
 typedef struct lbm_wenoc lbm_wenoc; /* opaque host-side handle */
 
@@ -65,7 +69,13 @@ typedef struct {
   double lf_alpha;           /* Lax-Friedrichs split speed; 0 selects settling_velocity + u_cap */
   double u_cap;              /* bound on |u_d| checked on the device; 0 selects 0.1 */
   double body_force[3];      /* extra uniform force (e.g. a channel flow), added to the buoyancy */
-  uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH | LW_FUSED_RK3 */
+  uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH | LW_FUSED_RK3
+                                | LW_SUGAR */
+  /* used with LW_SUGAR only (S normalised by its lower-layer value S0) */
+  double sugar_contrast;     /* S* = rho(S0)/rho_0 - 1 (Eq. S_star): force -gravity*S* S (1 - phi0 c) e_v */
+  double sugar_diffusivity;  /* D_s >= 0 */
+  double phi0;               /* particle volume fraction at c = 1, in the (1 - phi) factor of Eq. forceterm */
+  double vs_sugar;           /* kS: settling velocity Vs (1 - kS S) (Eq. stokes_vel with rho(S)) */
 } lbm_wenoc_params;
 
 /* Bytes of device workspace a handle with these parameters needs (populations,
@@ -188,6 +198,13 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b);
 int lbm_wenoc_gradient_workspace_bytes(const lbm_wenoc_params* p, int64_t nsteps, int32_t segment, size_t* bytes);
 int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t segment, void* adj_workspace,
                                size_t bytes, void* grad_c0, double* dJ_dVs, double* J);
+
+/* Sugar field (LW_SUGAR handles): set after lbm_wenoc_init (which zeroes it) and before
+ * or between steps, and read back; nx*ny(*nz) elements of the handle's element type, host
+ * or device memory, natural layout.  LW_EINVAL without LW_SUGAR, LW_ESTATE before init.
+ * Both synchronise. */
+int lbm_wenoc_set_sugar(lbm_wenoc* h, const void* S0);
+int lbm_wenoc_sugar(lbm_wenoc* h, void* S_out);
 
 /* Sum of a concentration field, FP64, for callers that cannot allocate device memory
  * (an application that owns a fixed device arena, a plugin inside another framework's

@@ -140,70 +140,94 @@ __global__ void __launch_bounds__(kAdjThreads) adj_faces_kernel(Args<T> a, AdjFi
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   const int nx = a.nx, ny = a.ny;
+  const unsigned n = (unsigned)a.n;  // 24 n < 2^31 (checked by the host)
   const T* __restrict__ cs = STAGE == 3 ? a.c2 : (STAGE == 2 ? a.c1 : a.c);
   const T* __restrict__ lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
+  const T* __restrict__ U = a.u;
   const T lscale = STAGE == 3 ? T(2.0 / 3.0) : (STAGE == 2 ? T(0.25) : T(1));
-  double vs_acc = 0.0;
+  T vs_acc = T(0);  // this thread's Vs terms (FP64 from the block sum on)
   if (x < nx) {
-    const long long n = a.n;
-    const long long node = (long long)y * nx + x;
+    const int node = y * nx + x;
+    const int row = node - x;
     const T alpha = a.alpha, ia = a.inv_alpha, kappa = a.kappa, vs = a.vs;
     const T lam_here = lscale * lsrc[node];
     // +x face (periodic)
     {
       T cv[6], wv[6], dc[6], dw[6];
+      if (x >= 2 && x + 3 < nx) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int p = wrap_any(x - 2 + k, nx);
-        cv[k] = cs[(long long)y * nx + p];
-        wv[k] = a.u[(long long)y * nx + p] * ia;
+        for (int k = 0; k < 6; ++k) {
+          cv[k] = cs[node - 2 + k];
+          wv[k] = U[node - 2 + k] * ia;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int q = row + wrap_any(x - 2 + k, nx);
+          cv[k] = cs[q];
+          wv[k] = U[q] * ia;
+        }
       }
-      const T lamF = lscale * lsrc[(long long)y * nx + (x + 1 == nx ? 0 : x + 1)] - lam_here;
+      const T lamF = lscale * lsrc[x + 1 == nx ? row : node + 1] - lam_here;
       face_adjoint<T>(cv, wv, alpha, kappa, lamF, dc, dw);
+      T* __restrict__ pc = fr.dcx + node;
+      T* __restrict__ pw = fr.dwx + node;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        fr.dcx[k * n + node] = dc[k];
-        fr.dwx[k * n + node] = dw[k];
+        pc[k * n] = dc[k];
+        pw[k * n] = dw[k];
       }
     }
-    // +y face (none on the lid row)
+    // +y face (none on the lid row); ghost rows beyond the floor and lid mirror c, flip u
+    T* __restrict__ pc = fr.dcy + node;
+    T* __restrict__ pw = fr.dwy + node;
     if (y < ny - 1) {
       T cv[6], wv[6], dc[6], dw[6];
+      const T* __restrict__ V = U + n;
+      if (y >= 2 && y + 3 < ny) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int p = y - 2 + k;
-        const bool ghost = p < 0 || p >= ny;
-        const int pr = p < 0 ? -1 - p : (p >= ny ? 2 * ny - 1 - p : p);
-        const long long q = (long long)pr * nx + x;
-        cv[k] = cs[q];
-        const T u = a.u[n + q];
-        wv[k] = ((ghost ? -u : u) - vs) * ia;
+        for (int k = 0; k < 6; ++k) {
+          const int q = node + (k - 2) * nx;
+          cv[k] = cs[q];
+          wv[k] = (V[q] - vs) * ia;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int p = y - 2 + k;
+          const bool ghost = p < 0 || p >= ny;
+          const int pr = p < 0 ? -1 - p : (p >= ny ? 2 * ny - 1 - p : p);
+          const int q = pr * nx + x;
+          cv[k] = cs[q];
+          const T u = V[q];
+          wv[k] = ((ghost ? -u : u) - vs) * ia;
+        }
       }
       const T lamF = lscale * lsrc[node + nx] - lam_here;
       face_adjoint<T>(cv, wv, alpha, kappa, lamF, dc, dw);
       T sw = T(0);
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        fr.dcy[k * n + node] = dc[k];
-        fr.dwy[k * n + node] = dw[k];
+        pc[k * n] = dc[k];
+        pw[k * n] = dw[k];
         sw += dw[k];
       }
-      vs_acc -= (double)sw;
+      vs_acc -= sw;
     } else {
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        fr.dcy[k * n + node] = T(0);
-        fr.dwy[k * n + node] = T(0);
+        pc[k * n] = T(0);
+        pw[k * n] = T(0);
       }
     }
     if (y == 0) {
       const T c0 = cs[node];
-      vs_acc += (double)c0 * (STAGE == 3 ? 2.0 / 3.0 : 1.0 / 6.0) - (double)(c0 * lam_here);
+      vs_acc += c0 * (STAGE == 3 ? T(2.0 / 3.0) : T(1.0 / 6.0)) - c0 * lam_here;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) vs_acc += __shfl_down_sync(0xffffffffu, vs_acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vs_acc;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)vs_acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -224,46 +248,69 @@ template <typename T, int STAGE>
 __device__ __forceinline__ void gather_node(const Args<T>& a, const AdjFields<T>& f, const FaceRecords<T>& fr,
                                             int x, int y, T& v, T& gx, T& gy) {
   const int nx = a.nx, ny = a.ny;
-  const long long n = a.n;
-  const long long node = (long long)y * nx + x;
+  const unsigned n = (unsigned)a.n;
+  const int node = y * nx + x;
+  const int row = node - x;
   const T* __restrict__ lsrc = STAGE == 3 ? f.mu : (STAGE == 2 ? f.lc2 : f.lc1);
   const T lscale = STAGE == 3 ? T(2.0 / 3.0) : (STAGE == 2 ? T(0.25) : T(1));
   const T vs = a.vs;
+  const T* __restrict__ DCX = fr.dcx;
+  const T* __restrict__ DWX = fr.dwx;
+  const T* __restrict__ DCY = fr.dcy;
+  const T* __restrict__ DWY = fr.dwy;
   T gc = T(0);
   gx = T(0);
   gy = T(0);
+  if (x >= 3 && x + 2 < nx) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const long long q = (long long)y * nx + wrap_any(x + 2 - k, nx);
-    gc += fr.dcx[k * n + q];
-    gx += fr.dwx[k * n + q];
-  }
+    for (int k = 0; k < 6; ++k) {
+      const unsigned q = k * n + (unsigned)(node + 2 - k);
+      gc += DCX[q];
+      gx += DWX[q];
+    }
+  } else {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const int yf = y + 2 - k;
-    if (yf >= 0 && yf <= ny - 2) {
-      const long long q = (long long)yf * nx + x;
-      gc += fr.dcy[k * n + q];
-      gy += fr.dwy[k * n + q];
+    for (int k = 0; k < 6; ++k) {
+      const unsigned q = k * n + (unsigned)(row + wrap_any(x + 2 - k, nx));
+      gc += DCX[q];
+      gx += DWX[q];
     }
   }
-  // ghost stencil positions folded onto the mirror rows (p = -1 -> 0, -2 -> 1, ny -> ny-1,
-  // ny+1 -> ny-2); face yf has position p at k = p - yf + 2
-  auto ghost = [&](int yf, int k) {
-    const long long q = (long long)yf * nx + x;
-    gc += fr.dcy[k * n + q];
-    gy -= fr.dwy[k * n + q];
-  };
-  if (y == 0) {
-    ghost(0, 1);
-    if (ny - 2 >= 1) ghost(1, 0);
+  if (y >= 3 && y + 4 <= ny) {  // faces y - 3 .. y + 2 all exist, no ghost lands here
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const unsigned q = k * n + (unsigned)(node + (2 - k) * nx);
+      gc += DCY[q];
+      gy += DWY[q];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int yf = y + 2 - k;
+      if (yf >= 0 && yf <= ny - 2) {
+        const unsigned q = k * n + (unsigned)(yf * nx + x);
+        gc += DCY[q];
+        gy += DWY[q];
+      }
+    }
+    // ghost stencil positions folded onto the mirror rows (p = -1 -> 0, -2 -> 1, ny -> ny-1,
+    // ny+1 -> ny-2); face yf has position p at k = p - yf + 2
+    auto ghost = [&](int yf, int k) {
+      const unsigned q = k * n + (unsigned)(yf * nx + x);
+      gc += DCY[q];
+      gy -= DWY[q];
+    };
+    if (y == 0) {
+      ghost(0, 1);
+      if (ny - 2 >= 1) ghost(1, 0);
+    }
+    if (y == 1) ghost(0, 0);
+    if (y == ny - 1) {
+      ghost(ny - 2, 4);
+      if (ny - 3 >= 0) ghost(ny - 3, 5);
+    }
+    if (y == ny - 2) ghost(ny - 2, 5);
   }
-  if (y == 1) ghost(0, 0);
-  if (y == ny - 1) {
-    ghost(ny - 2, 4);
-    if (ny - 3 >= 0) ghost(ny - 3, 5);
-  }
-  if (y == ny - 2) ghost(ny - 2, 5);
   const T lam_here = lscale * lsrc[node];
   v = lam_here + gc;
   if (STAGE == 1) v += T(1.0 / 3.0) * f.mu[node] + T(0.75) * f.lc2[node];

@@ -32,7 +32,20 @@ struct Args {
   T alpha;           // Lax-Friedrichs split speed
   T inv_alpha;
   T u_cap;
+  // sugar (the paper's density-altering scalar), null S when off
+  const T* S;  // S of step n
+  T* S2;       // S of step n + 1
+  T gS;        // gravity * sugar_contrast (S*): force -gS S (1 - phi0 c) along the vertical
+  T phi0;      // particle volume fraction at c = 1
+  T ks;        // settling velocity Vs (1 - ks S)
+  T Ds;        // sugar diffusivity
 };
+
+// Settling velocity at node m: Vs, or Vs (1 - ks S_m) with sugar.
+template <typename T>
+__device__ __forceinline__ T settling_at(const Args<T>& a, long long m) {
+  return a.S ? a.vs * (T(1) - a.ks * a.S[m]) : a.vs;
+}
 
 __device__ __forceinline__ int wrap_dec(int a, int n) { return a < 0 ? a + n : a; }
 __device__ __forceinline__ int wrap_inc(int a, int n) { return a >= n ? a - n : a; }

@@ -68,12 +68,16 @@ __device__ __forceinline__ void load_populations(const Args<T>& a, int x, int y,
   }
 }
 
+// Force at a node: body force - A c along the vertical, and with sugar also
+// - g S* S (1 - phi0 c) (the density-altering term of the force).
 template <class LAT, typename T>
-__device__ __forceinline__ void node_force(const Args<T>& a, T cval, T (&F)[3]) {
+__device__ __forceinline__ void node_force(const Args<T>& a, long long node, T (&F)[3]) {
+  const T cval = a.c[node];
   F[0] = a.bf[0];
   F[1] = a.bf[1];
   F[2] = a.bf[2];
   F[LAT::VAXIS] -= a.A * cval;
+  if (a.S) F[LAT::VAXIS] -= a.gS * a.S[node] * (T(1) - a.phi0 * cval);
 }
 
 template <class LAT, typename T, int PARITY>
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
     if (LAT::cz(i)) j[2] += LAT::cz(i) * g[i];
   }
   T F[3];
-  node_force<LAT, T>(a, a.c[node], F);
+  node_force<LAT, T>(a, node, F);
   const T rho = T(1) + drho;
   const T inv_rho = T(1) / rho;
   T u[3];
@@ -145,12 +149,12 @@ __global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
 // a row taken once per block (a block is one row segment), and streaming cache
 // hints on the population traffic (each population is touched once per step), so
 // that c and u stay in L2 for the transport kernel that follows.
-template <typename T, int PARITY, bool RHO = false>
+template <typename T, int PARITY, bool RHO = false, bool SUGAR = false>
 __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out = nullptr);
 
-template <typename T, int PARITY>
+template <typename T, int PARITY, bool SUGAR = false>
 __global__ void __launch_bounds__(128) lbm_d2q9_kernel(Args<T> a) {
-  lbm_d2q9_body<T, PARITY>(a, blockIdx.x, blockIdx.y);
+  lbm_d2q9_body<T, PARITY, false, SUGAR>(a, blockIdx.x, blockIdx.y);
 }
 
 // The same step that also stores rho (the steps recorded for the adjoint).
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(128) lbm_d2q9_record_kernel(Args<T> a, T* rho_
 }
 
 // Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.
-template <typename T, int PARITY, bool RHO>
+template <typename T, int PARITY, bool RHO, bool SUGAR>
 __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out) {
   const int x = bx * blockDim.x + threadIdx.x;
   const int y = by;
@@ -203,7 +207,10 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, 
     if (D2Q9::cx(i)) jx += D2Q9::cx(i) * g[i];
     if (D2Q9::cy(i)) jy += D2Q9::cy(i) * g[i];
   }
-  const T Fx = a.bf[0], Fy = a.bf[1] - a.A * a.c[node];
+  const T cn = a.c[node];
+  T Fy = a.bf[1] - a.A * cn;
+  if (SUGAR) Fy -= a.gS * a.S[node] * (T(1) - a.phi0 * cn);
+  const T Fx = a.bf[0];
   const T rho = T(1) + drho;
   const T inv_rho = T(1) / rho;
   const T ux = (jx + T(0.5) * Fx) * inv_rho, uy = (jy + T(0.5) * Fy) * inv_rho;
@@ -250,7 +257,7 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, 
 // neighbour offsets along x, y (periodic) and z (walls or periodic) hoisted, the wall
 // tests taken once per block (a block is one x segment of one (y, z) row), streaming
 // cache hints on the population traffic.
-template <typename T, int PARITY>
+template <typename T, int PARITY, bool SUGAR = false>
 __global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -294,7 +301,10 @@ __global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
     if (D3Q19::cy(i)) jy += D3Q19::cy(i) * g[i];
     if (D3Q19::cz(i)) jz += D3Q19::cz(i) * g[i];
   }
-  const T Fx = a.bf[0], Fy = a.bf[1], Fz = a.bf[2] - a.A * a.c[node];
+  const T cn = a.c[node];
+  T Fz = a.bf[2] - a.A * cn;
+  if (SUGAR) Fz -= a.gS * a.S[node] * (T(1) - a.phi0 * cn);
+  const T Fx = a.bf[0], Fy = a.bf[1];
   const T rho = T(1) + drho;
   const T inv_rho = T(1) / rho;
   const T ux = (jx + T(0.5) * Fx) * inv_rho, uy = (jy + T(0.5) * Fy) * inv_rho, uz = (jz + T(0.5) * Fz) * inv_rho;
@@ -356,7 +366,7 @@ __global__ void __launch_bounds__(128) fields_kernel(Args<T> a, T* rho_out, T* u
     j[2] += LAT::cz(i) * g[i];
   }
   T F[3];
-  node_force<LAT, T>(a, a.c[node], F);
+  node_force<LAT, T>(a, node, F);
   const T rho = T(1) + drho;
   if (rho_out) rho_out[node] = rho;
   if (u_out) {

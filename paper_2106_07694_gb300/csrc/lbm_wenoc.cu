@@ -53,7 +53,7 @@ static_assert(lattice_ok<D3Q19>(), "D3Q19 table");
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t g, c, c1, c2, u, partials, scalars, status, total;
+  size_t g, c, c1, c2, u, partials, scalars, status, sa, sb, total;
 };
 
 Layout make_layout(const lbm_wenoc_params& p) {
@@ -75,6 +75,9 @@ Layout make_layout(const lbm_wenoc_params& p) {
   L.partials = take(sizeof(double) * lw::kMaxReduceBlocks);
   L.scalars = take(sizeof(double) * 4);
   L.status = take(sizeof(unsigned) * 4);
+  const bool sugar = (p.flags & LW_SUGAR) != 0;
+  L.sa = take(sugar ? n * es : 0);  // sugar of step n and n + 1 (ping-pong)
+  L.sb = take(sugar ? n * es : 0);
   L.total = off;
   return L;
 }
@@ -89,6 +92,10 @@ int check_params(const lbm_wenoc_params* p) {
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LW_EINVAL;  // stability needs tau > 1/2
   if (!(p->settling_velocity >= 0.0) || !(p->diffusivity >= 0.0)) return LW_EINVAL;
   if (!(p->lf_alpha >= 0.0) || !(p->u_cap >= 0.0)) return LW_EINVAL;
+  if ((p->flags & LW_SUGAR) && ((p->flags & LW_FUSED_RK3) || !(p->sugar_diffusivity >= 0.0) ||
+                                !std::isfinite(p->sugar_contrast) || !std::isfinite(p->phi0) ||
+                                !std::isfinite(p->vs_sugar)))
+    return LW_EINVAL;
   const double nn = (double)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   if (nn > 4.0e9) return LW_EINVAL;
   if ((double)(p->dim == 2 ? 9 : 19) * nn >= 2147483647.0) return LW_EINVAL;  // 32-bit population offsets
@@ -106,7 +113,7 @@ struct lbm_wenoc {
   bool fp64 = false, walls = true, frozen = false, use_graphs = true;
   long long n = 0;
   int parity = 0;  // AA-pattern parity of the population array
-  int cur = 0;     // which buffer holds c^n: 0 = c, 1 = c1 (2D FP32 sweep path ping-pongs)
+  int cur = 0;     // ping-pong index: c^n in c or c1 (fused sweep), S^n in sa or sb (sugar)
   bool sweep = false;
   lw::SweepLaunch sweep_geom{};
   bool sweep3d = false;  // 3D FP32 with walls: tiled z-sweep stage kernels
@@ -114,6 +121,7 @@ struct lbm_wenoc {
   bool stage2d = false;  // 2D FP32 with walls: three row-sweep stage kernels
   int stage2d_rows = 0;
   bool initialised = false;
+  bool sugar = false;  // LW_SUGAR: S in L.sa / L.sb, selected by cur (the generic transport path)
   int64_t steps = 0;
   int64_t launches = 0;
   double alpha = 0.0;
@@ -141,7 +149,7 @@ Args<T> make_args(const lbm_wenoc* h) {
   Args<T> a{};
   unsigned char* b = h->ws;
   a.g = reinterpret_cast<T*>(b + h->L.g);
-  a.c = reinterpret_cast<T*>(b + (h->cur ? h->L.c1 : h->L.c));
+  a.c = reinterpret_cast<T*>(b + (h->sweep && h->cur ? h->L.c1 : h->L.c));
   a.c1 = reinterpret_cast<T*>(b + h->L.c1);
   a.c2 = reinterpret_cast<T*>(b + h->L.c2);
   a.u = reinterpret_cast<T*>(b + h->L.u);
@@ -164,17 +172,25 @@ Args<T> make_args(const lbm_wenoc* h) {
   a.alpha = T(h->alpha);
   a.inv_alpha = T(1.0 / h->alpha);
   a.u_cap = T(p.u_cap);
+  if (h->sugar) {
+    a.S = reinterpret_cast<T*>(b + (h->cur ? h->L.sb : h->L.sa));
+    a.S2 = reinterpret_cast<T*>(b + (h->cur ? h->L.sa : h->L.sb));
+    a.gS = T(p.gravity * p.sugar_contrast);
+    a.phi0 = T(p.phi0);
+    a.ks = T(p.vs_sugar);
+    a.Ds = T(p.sugar_diffusivity);
+  }
   return a;
 }
 
 // Kernel families for timing.
 enum Kind {
   K_LBM = 0, K_STAGE1, K_STAGE2, K_STAGE3, K_DEPOSIT, K_RK3_SWEEP, K_OTHER,
-  K_ADJ_FACES, K_ADJ_GATHER, K_ADJ_FLUID, K_COUNT
+  K_ADJ_FACES, K_ADJ_GATHER, K_ADJ_FLUID, K_SUGAR, K_COUNT
 };
 const char* kKindNames[K_COUNT] = {"lbm_collide_stream", "rk_stage1",  "rk_stage2",  "rk_stage3",
                                    "deposit_reduce",     "rk3_sweep2d", "other",     "adj_faces",
-                                   "adj_gather",         "adj_gather_fluid"};
+                                   "adj_gather",         "adj_gather_fluid", "sugar_upwind"};
 // The 3D FP32 stage kernels are timed under the rk_stage* names.
 
 cudaEvent_t take_event(lbm_wenoc* h) {
@@ -234,12 +250,18 @@ void enqueue_step(lbm_wenoc* h, int parity) {
   if (!h->frozen) {
     launch(h, K_LBM, [&] {
       if (LAT::DIM == 2) {
-        if (parity == 0)
+        if (h->sugar)
+          parity == 0 ? lw::lbm_d2q9_kernel<T, 0, true><<<grd, blk, 0, s>>>(a)
+                      : lw::lbm_d2q9_kernel<T, 1, true><<<grd, blk, 0, s>>>(a);
+        else if (parity == 0)
           lw::lbm_d2q9_kernel<T, 0><<<grd, blk, 0, s>>>(a);
         else
           lw::lbm_d2q9_kernel<T, 1><<<grd, blk, 0, s>>>(a);
       } else {
-        if (parity == 0)
+        if (h->sugar)
+          parity == 0 ? lw::lbm_d3q19_kernel<T, 0, true><<<grd, blk, 0, s>>>(a)
+                      : lw::lbm_d3q19_kernel<T, 1, true><<<grd, blk, 0, s>>>(a);
+        else if (parity == 0)
           lw::lbm_d3q19_kernel<T, 0><<<grd, blk, 0, s>>>(a);
         else
           lw::lbm_d3q19_kernel<T, 1><<<grd, blk, 0, s>>>(a);
@@ -290,6 +312,10 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
       lw::deposit_kernel<T><<<dep_blocks, lw::kReduceThreads, 0, s>>>(a, nfloor);
     });
   launch(h, K_STAGE3, [&] { lw::rk_stage_kernel<T, LAT::DIM, 3><<<grd, blk, 0, s>>>(a); });
+  if (h->sugar) {  // S^{n+1} from S^n and u^n into the other buffer
+    launch(h, K_SUGAR, [&] { lw::sugar_kernel<T, LAT::DIM><<<grd, blk, 0, s>>>(a); });
+    h->cur ^= 1;
+  }
 }
 
 void enqueue_one(lbm_wenoc* h, int parity) {
@@ -340,7 +366,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
 int launches_per_step(const lbm_wenoc* h) {
   if (h->sweep) return h->frozen ? 1 : 2;
   if (h->stage2d) return (h->frozen ? 0 : 1) + 3;
-  return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0);
+  return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0) + (h->sugar ? 1 : 0);
 }
 
 int sync_and_status(lbm_wenoc* h) {
@@ -418,13 +444,14 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   h->fp64 = (p->flags & LW_FP64) != 0;
   h->walls = (p->flags & LW_PERIODIC_VERTICAL) == 0;
   h->frozen = (p->flags & LW_FROZEN_VELOCITY) != 0;
+  h->sugar = (p->flags & LW_SUGAR) != 0;
   h->use_graphs = (p->flags & LW_NO_GRAPH) == 0;
   h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : p->settling_velocity + h->p.u_cap;
   cudaGetDevice(&h->device);
   h->sweep = !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
-  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
+  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep && !h->sugar &&
                (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
   if (h->stage2d) {
     int sms = 0;
@@ -441,7 +468,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
       return LW_ECUDA;
     }
   }
-  h->sweep3d = !h->fp64 && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
+  h->sweep3d = !h->fp64 && h->p.dim == 3 && !h->sugar && lw::sweep3d_supported(h->p.nz, h->walls);
   if (h->sweep3d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
@@ -476,6 +503,7 @@ int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
   }
   if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
   if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (h->sugar && cudaMemsetAsync(h->ws + h->L.sa, 0, cbytes, h->stream) != cudaSuccess) return LW_ECUDA;
   if (h->p.dim == 2) {
     if (h->fp64)
       launch_init<D2Q9, double>(h, static_cast<const double*>(u0dev));
@@ -523,7 +551,7 @@ int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
       if (cudaGraphLaunch(*slot, h->stream) != cudaSuccess) return LW_ECUDA;
       h->launches += (int64_t)per_step * count;
       if (!h->frozen) h->parity = (h->parity + count) & 1;
-      if (h->sweep) h->cur = (h->cur + count) & 1;
+      if (h->sweep || h->sugar) h->cur = (h->cur + count) & 1;
       h->steps += count;
       left -= count;
     }
@@ -605,7 +633,7 @@ int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
   };
   if (rho && !copy_out(rho, rho_dev, cbytes)) return LW_ECUDA;
   if (u && !copy_out(u, u_dev, cbytes * h->p.dim)) return LW_ECUDA;
-  if (c && !copy_out(c, h->ws + (h->cur ? h->L.c1 : h->L.c), cbytes)) return LW_ECUDA;
+  if (c && !copy_out(c, h->ws + (h->sweep && h->cur ? h->L.c1 : h->L.c), cbytes)) return LW_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
   return LW_OK;
 }
@@ -618,6 +646,26 @@ int lbm_wenoc_status(lbm_wenoc* h) {
 int64_t lbm_wenoc_steps(const lbm_wenoc* h) { return h ? h->steps : -1; }
 
 int64_t lbm_wenoc_launch_count(const lbm_wenoc* h) { return h ? h->launches : -1; }
+
+int lbm_wenoc_set_sugar(lbm_wenoc* h, const void* S0) {
+  if (!h || !S0 || !h->sugar) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const size_t bytes = (size_t)h->n * (h->fp64 ? 8 : 4);
+  cudaMemcpyKind k = is_device_pointer(S0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(h->ws + (h->cur ? h->L.sb : h->L.sa), S0, bytes, k, h->stream) != cudaSuccess)
+    return LW_ECUDA;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+int lbm_wenoc_sugar(lbm_wenoc* h, void* S_out) {
+  if (!h || !S_out || !h->sugar) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const size_t bytes = (size_t)h->n * (h->fp64 ? 8 : 4);
+  cudaMemcpyKind k = is_device_pointer(S_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (cudaMemcpyAsync(S_out, h->ws + (h->cur ? h->L.sb : h->L.sa), bytes, k, h->stream) != cudaSuccess)
+    return LW_ECUDA;
+  return sync_and_status(h);
+}
 
 int lbm_wenoc_profile_enable(lbm_wenoc* h, int enable) {
   if (!h) return LW_EINVAL;
@@ -704,7 +752,7 @@ namespace {
 
 bool batch_params_ok(const lbm_wenoc_params& p) {
   return check_params(&p) == LW_OK && p.dim == 2 && !(p.flags & LW_FP64) && !(p.flags & LW_PERIODIC_VERTICAL) &&
-         !(p.flags & LW_FROZEN_VELOCITY) && !(p.flags & LW_FUSED_RK3) &&
+         !(p.flags & LW_FROZEN_VELOCITY) && !(p.flags & LW_FUSED_RK3) && !(p.flags & LW_SUGAR) &&
          (p.nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
 }
 
@@ -956,7 +1004,7 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
 namespace {
 
 bool gradient_params_ok(const lbm_wenoc* h) {
-  return h && h->p.dim == 2 && h->walls && !h->frozen && !h->sweep && h->p.lf_alpha > 0.0;
+  return h && h->p.dim == 2 && h->walls && !h->frozen && !h->sweep && !h->sugar && h->p.lf_alpha > 0.0;
 }
 
 struct GradLayout {
@@ -1156,6 +1204,7 @@ int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int
                                size_t bytes, void* grad_c0, double* dJ_dVs, double* J) {
   if (!h || !c0 || !grad_c0 || !dJ_dVs || !J || nsteps < 1 || segment < 1 || !adj_workspace) return LW_EINVAL;
   if (!gradient_params_ok(h)) return LW_EINVAL;
+  if (24.0 * (double)h->n >= 2147483647.0) return LW_EINVAL;  // 32-bit offsets of the face records
   if ((reinterpret_cast<uintptr_t>(adj_workspace) & 255u) != 0) return LW_EINVAL;
   segment = (int32_t)std::min<int64_t>(segment, nsteps);
   const GradLayout G = grad_layout(h->p, nsteps, segment);

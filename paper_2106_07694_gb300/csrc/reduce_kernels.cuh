@@ -53,10 +53,11 @@ __global__ void __launch_bounds__(kReduceThreads) deposit_kernel(Args<T> a, long
   double acc = 0.0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nfloor;
        k += (long long)gridDim.x * blockDim.x) {
-    acc += ((double)a.c[k] + (double)a.c1[k]) * (1.0 / 6.0) + (double)a.c2[k] * (2.0 / 3.0);
+    const double b = ((double)a.c[k] + (double)a.c1[k]) * (1.0 / 6.0) + (double)a.c2[k] * (2.0 / 3.0);
+    acc += a.S ? (double)settling_at(a, k) * b : b;  // with sugar Vs(S) per floor node
   }
   double s = block_sum(acc, sh);
-  finish_reduction(s * (double)a.vs, a.partials, a.ticket, &a.scalars[0], 1);
+  finish_reduction(a.S ? s : s * (double)a.vs, a.partials, a.ticket, &a.scalars[0], 1);
 }
 
 // scalars[1] = sum of src[0..count)

@@ -67,7 +67,6 @@ __device__ __forceinline__ T face_flux(const Args<T>& a, const T* __restrict__ c
   const long long stride[3] = {1, a.nx, (long long)a.nx * a.ny};
   const long long base = ((long long)z * a.ny + y) * a.nx + x - (long long)pos0[d] * stride[d];
   const bool wall_axis = (d == VA) && a.walls;
-  const T sv = (d == VA) ? a.vs : T(0);
   T hp[6], hm[6], cv[6];
 #pragma unroll
   for (int k = -2; k <= 3; ++k) {
@@ -88,7 +87,8 @@ __device__ __forceinline__ T face_flux(const Args<T>& a, const T* __restrict__ c
     const T cval = cin[m];
     T ud = a.u[(long long)d * a.n + m];
     if (ghost) ud = -ud;
-    const T ws = (ud - sv) * a.inv_alpha;  // w / alpha
+    const T sv = (d == VA) ? settling_at(a, m) : T(0);  // Vs, or Vs(S) with sugar
+    const T ws = (ud - sv) * a.inv_alpha;               // w / alpha
     cv[k + 2] = cval;
     hp[k + 2] = T(0.5) * (ws + T(1)) * cval;
     hm[k + 2] = T(0.5) * (ws - T(1)) * cval;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128) rk_stage_kernel(Args<T> a) {
     else
       fplus = face_flux<T, DIM>(a, cin, x, y, z, d);
     if (wall_axis && pos[d] == 0) {
-      fminus = -a.vs * cin[node];  // floor: settling outflow
+      fminus = -settling_at(a, node) * cin[node];  // floor: settling outflow
     } else {
       int q[3] = {x, y, z};
       q[d] = wrap_dec(pos[d] - 1, ext[d]);
@@ -143,6 +143,43 @@ __global__ void __launch_bounds__(128) rk_stage_kernel(Args<T> a) {
     a.c[node] = out;
     report_status(a.status, !finite_val(out));
   }
+}
+
+// Sugar (the paper's density-altering scalar): one explicit first-order upwind step per
+// axis in the advective form of Supplement Eqs. S5 (u > 0: backward difference) and S6
+// (u < 0: forward difference), with the velocity of this step's fluid update, plus
+// central diffusion D_s; walls mirror S (Neumann).  Writes S2.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) sugar_kernel(Args<T> a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx) return;
+  const int VA = DIM - 1;
+  const long long node = ((long long)z * a.ny + y) * a.nx + x;
+  const int pos[3] = {x, y, z};
+  const int ext[3] = {a.nx, a.ny, a.nz};
+  const long long stride[3] = {1, a.nx, (long long)a.nx * a.ny};
+  const T s0 = a.S[node];
+  T next = s0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const bool wall_axis = (d == VA) && a.walls;
+    int pm = pos[d] - 1, pp = pos[d] + 1;
+    if (wall_axis) {
+      pm = pm < 0 ? 0 : pm;                       // mirror ghost below the floor
+      pp = pp >= ext[d] ? ext[d] - 1 : pp;        // and above the lid
+    } else {
+      pm = wrap_any(pm, ext[d]);
+      pp = wrap_any(pp, ext[d]);
+    }
+    const T sm = a.S[node + (long long)(pm - pos[d]) * stride[d]];
+    const T sp = a.S[node + (long long)(pp - pos[d]) * stride[d]];
+    const T u = a.u[(long long)d * a.n + node];
+    next -= u > T(0) ? u * (s0 - sm) : u * (sp - s0);
+    next += a.Ds * (sp - T(2) * s0 + sm);
+  }
+  a.S2[node] = next;
 }
 
 }  // namespace lw

@@ -26,6 +26,7 @@ LW_PERIODIC_VERTICAL = 0x2
 LW_FROZEN_VELOCITY = 0x4
 LW_NO_GRAPH = 0x8
 LW_FUSED_RK3 = 0x10
+LW_SUGAR = 0x20
 
 _ERRORS = {LW_EINVAL: "LW_EINVAL", LW_ENOMEM: "LW_ENOMEM", LW_ECUDA: "LW_ECUDA",
            LW_EUNSTABLE: "LW_EUNSTABLE", LW_ETIMEOUT: "LW_ETIMEOUT", LW_ESTATE: "LW_ESTATE"}
@@ -38,7 +39,8 @@ EXPORTED = [
     "lbm_wenoc_destroy", "lbm_wenoc_batch_workspace_bytes", "lbm_wenoc_batch_create",
     "lbm_wenoc_batch_instance", "lbm_wenoc_batch_step", "lbm_wenoc_batch_autotune",
     "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy",
-    "lbm_wenoc_gradient_workspace_bytes", "lbm_wenoc_deposit_gradient",
+    "lbm_wenoc_gradient_workspace_bytes", "lbm_wenoc_deposit_gradient", "lbm_wenoc_set_sugar",
+    "lbm_wenoc_sugar",
 ]
 
 
@@ -63,6 +65,10 @@ class lbm_wenoc_params(ctypes.Structure):
         ("u_cap", ctypes.c_double),
         ("body_force", ctypes.c_double * 3),
         ("flags", ctypes.c_uint32),
+        ("sugar_contrast", ctypes.c_double),
+        ("sugar_diffusivity", ctypes.c_double),
+        ("phi0", ctypes.c_double),
+        ("vs_sugar", ctypes.c_double),
     ]
 
 
@@ -120,6 +126,8 @@ def load():
     L.lbm_wenoc_gradient_workspace_bytes.argtypes = [P, i64, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
     dp = ctypes.POINTER(ctypes.c_double)
     L.lbm_wenoc_deposit_gradient.argtypes = [vp, vp, i64, ctypes.c_int32, vp, ctypes.c_size_t, vp, dp, dp]
+    L.lbm_wenoc_set_sugar.argtypes = [vp, vp]
+    L.lbm_wenoc_sugar.argtypes = [vp, vp]
     for name in EXPORTED:
         if name not in ("lbm_wenoc_steps", "lbm_wenoc_launch_count", "lbm_wenoc_destroy",
                         "lbm_wenoc_batch_instance", "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy"):
@@ -238,6 +246,14 @@ def lbm_wenoc_deposit_gradient(h, c0, nsteps, segment, workspace, nbytes, grad_c
     return J.value, dvs.value
 
 
+def lbm_wenoc_set_sugar(h, S0):
+    return _check("lbm_wenoc_set_sugar", load().lbm_wenoc_set_sugar(h, _ptr(S0)))
+
+
+def lbm_wenoc_sugar(h, S_out):
+    return _check("lbm_wenoc_sugar", load().lbm_wenoc_sugar(h, _ptr(S_out)))
+
+
 def default_segment(nsteps):
     """Checkpoint spacing that minimises the stored states (checkpoints + one segment)."""
     return max(1, int(round(float(nsteps) ** 0.5)))
@@ -252,7 +268,8 @@ def lbm_wenoc_destroy(h):
 
 def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0,
                 diffusivity=0.0, lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), fp64=False,
-                periodic_vertical=False, frozen_velocity=False, graphs=True, fused_rk3=False):
+                periodic_vertical=False, frozen_velocity=False, graphs=True, fused_rk3=False,
+                sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0):
     p = lbm_wenoc_params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -263,7 +280,8 @@ def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velo
         p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
     p.flags = ((LW_FP64 if fp64 else 0) | (LW_PERIODIC_VERTICAL if periodic_vertical else 0) |
                (LW_FROZEN_VELOCITY if frozen_velocity else 0) | (0 if graphs else LW_NO_GRAPH) |
-               (LW_FUSED_RK3 if fused_rk3 else 0))
+               (LW_FUSED_RK3 if fused_rk3 else 0) | (LW_SUGAR if sugar else 0))
+    p.sugar_contrast, p.sugar_diffusivity, p.phi0, p.vs_sugar = sugar_contrast, sugar_diffusivity, phi0, vs_sugar
     return p
 
 
@@ -339,6 +357,17 @@ class Simulation:
 
     def status(self):
         return lbm_wenoc_status(self.handle)
+
+    def set_sugar(self, S0):
+        """Sugar field of a sugar=True handle (after init)."""
+        S = self._as_input(S0, self.grid)
+        lbm_wenoc_set_sugar(self.handle, S)
+
+    def sugar(self, device="cpu"):
+        import torch
+        S = torch.empty(self.grid, dtype=self.dtype, device=device)
+        lbm_wenoc_sugar(self.handle, S)
+        return S
 
     def deposit_gradient(self, c0, nsteps, segment=None):
         """Run nsteps from c0 (fluid at rest) and return (J, dJ/dc0, dJ/dVs): J the
