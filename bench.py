@@ -29,6 +29,8 @@ from paper_2106_07694_gb300 import workloads  # noqa: E402
 WORKLOADS = {
     "2d": (workloads.MAIN_2D, "coupled LBM+WENO5 GLUPS (2D D2Q9 2048x4096 FP32)", "D2Q9"),
     "3d": (workloads.MAIN_3D, "coupled LBM+WENO5 GLUPS (3D D3Q19 256x256x512 FP32)", "D3Q19"),
+    "sugar": (workloads.SUGAR_2D, "coupled LBM+WENO5+sugar GLUPS (2D D2Q9 2048x4096 FP32, two-layer state)",
+              "D2Q9"),
 }
 WL, METRIC, LATTICE = WORKLOADS["2d"]
 ADJOINT_METRIC = ("gradient of the deposited mass wrt c0 and Vs, GLUPS of the reverse-mode pass "
@@ -53,7 +55,7 @@ def fp32_peak_tflops(clk):
 
 def phys_kwargs(wl):
     return dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
-                settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity)
+                settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity, **wl.sugar)
 
 
 def load_peaks():
@@ -153,6 +155,8 @@ def run_oracle_sample(wl, steps, threads):
         wl = wl.with_(shape=(wl.shape[0], wl.shape[1], 64))
     s = oracle.OracleSim(wl.shape, **phys_kwargs(wl))
     s.init(wl.initial_c())
+    if wl.sugar:
+        s.set_sugar(wl.initial_S())
     s.step(1)
     t0 = time.perf_counter()
     s.step(steps)
@@ -174,6 +178,8 @@ def bench_reference(args):
     band = WL.with_(shape=tuple(WL.shape[:-1]) + ((128 if len(WL.shape) == 2 else 32),))
     s = oracle.OracleSim(band.shape, **phys_kwargs(band))
     s.init(band.initial_c())
+    if band.sugar:
+        s.set_sugar(band.initial_S())
     s.step(args.warmup)
     t0 = time.perf_counter()
     s.step(args.steps)
@@ -218,7 +224,10 @@ def bench_ours(args):
     stream = torch.cuda.current_stream()
     sim = lw.Simulation(wl.shape, fp64=False, stream=stream, **kw)
     c0 = wl.initial_c().astype(np.float32)
+    S0 = wl.initial_S().astype(np.float32) if wl.sugar else None
     sim.init(torch.from_numpy(c0).to(dev))
+    if S0 is not None:
+        sim.set_sugar(torch.from_numpy(S0).to(dev))
     sim.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -264,14 +273,15 @@ def bench_ours(args):
     #   whole step     populations in and out + c in and out: 80 B (2D), 160 B (3D)
     # FP32 peak: 152 SMs x 128 lanes x 2 flop (FMA) x the sampled SM clock.
     dim = len(wl.shape)
-    lbm_B = 2 * (9 if dim == 2 else 19) * 4 + 4
-    step_B = lbm_B + 4
+    lbm_B = 2 * (9 if dim == 2 else 19) * 4 + 4 + (4 if wl.sugar else 0)  # + S in (sugar force)
+    step_B = lbm_B + 4 + (4 if wl.sugar else 0)                               # + c out (+ S out)
     tr_flop = 915.0 if dim == 2 else 1371.0
     flop_of = {"rk3_sweep2d": tr_flop, "rk3_sweep3d": tr_flop, "rk_stage1": tr_flop / 3,
                "rk_stage2": tr_flop / 3, "rk_stage3": tr_flop / 3}
     sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
-    ncu_traffic = {k: kernel_traffic(k) if dim == 2 else None for k in NCU_TRAFFIC}
+    # ncu traffic was captured on the plain 2D workload's kernels only
+    ncu_traffic = {k: kernel_traffic(k) if wl is workloads.MAIN_2D else None for k in NCU_TRAFFIC}
 
     def avg_s(name):
         n_, t_ = stats[name]
@@ -311,13 +321,18 @@ def bench_ours(args):
     # K steps, deposit read and D2H of the final c field, all inside the timed region
     c_host = torch.from_numpy(c0).pin_memory()
     c_out = torch.empty_like(c_host).pin_memory()
+    S_host = torch.from_numpy(S0).pin_memory() if S0 is not None else None
     sim2 = lw.Simulation(wl.shape, fp64=False, stream=stream, **kw)
     sim2.init(c_host)
+    if S_host is not None:
+        sim2.set_sugar(S_host)
     sim2.step(1)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     sim2.init(c_host)
+    if S_host is not None:
+        sim2.set_sugar(S_host)
     sim2.step(args.steps)
     dep = sim2.deposit
     lw.lbm_wenoc_fields(sim2.handle, None, None, c_out)
@@ -325,9 +340,9 @@ def bench_ours(args):
     barrier()
     e2e_s = job_time_ms(e2e_s * 1e3, device=dev) * 1e-3
     e2e = {"value": world * wl.nodes * args.steps / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": c_host.numel() * 4 / args.steps,
+           "h2d_bytes_per_step": (c_host.numel() * 4 * (2 if S_host is not None else 1)) / args.steps,
            "d2h_bytes_per_step": (c_out.numel() * 4 + 8) / args.steps,
-           "note": "per job: H2D c0 + init + K steps + deposit (8 B) + D2H c, host wall clock"}
+           "note": "per job: H2D c0 (+ S0) + init + K steps + deposit (8 B) + D2H c, host wall clock"}
     assert np.isfinite(dep)
     sim2.close()
 
@@ -347,7 +362,7 @@ def bench_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "shape": list(wl.shape), "lattice": LATTICE,
                        "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
-                       "kappa": wl.diffusivity, "parallelism": f"replicas{world}",
+                       "kappa": wl.diffusivity, "parallelism": f"replicas{world}", **({"sugar": wl.sugar} if wl.sugar else {}),
                        "l2": f"inputs larger than L2 (populations {wl.nodes * (9 if len(wl.shape) == 2 else 19) * 4 / 1e6:.0f} MB)"},
             "roofline": roofline, "lbm_roofline": lbm_roofline, "transport_roofline": transport_roofline,
             "step_roofline": step_roofline,
@@ -550,7 +565,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=0, help="override the horizon (profiling only)")
     ap.add_argument("--adjoint-segment", type=int, default=0, help="override the checkpoint spacing")
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batch", "adjoint"],
-                    help="2d: the 2048x4096 D2Q9 case the metric is quoted on; 3d: 256x256x512 D3Q19")
+                    help="2d: the 2048x4096 D2Q9 case the metric is quoted on; 3d: 256x256x512 D3Q19; "
+                         "sugar: the 2048x4096 case with the sugar scalar; batch; adjoint")
     args = ap.parse_args()
     global WL, METRIC, LATTICE
     if args.workload == "batch":

@@ -1,5 +1,6 @@
-"""Linear stability analysis of the settling interface (Sec. 3), reduced to one
-transported scalar (no density-altering scalar: S* = 0), in lattice units.
+"""Linear stability analysis of the settling interface (Sec. 3), in lattice units:
+``growth_rate`` with one transported scalar (no density-altering scalar: S* = 0) and
+``growth_rate_sugar`` with the sugar scalar S as well (the paper's full K/W problem).
 
 TEST INFRASTRUCTURE ONLY (reference for the coupled early-time growth rate).
 
@@ -79,6 +80,69 @@ def growth_rate(k, H, nu, A, kappa, vs, cbar_fn, m=400):
     Ccp[1:-1, :] = 1j * k * np.diag(dcb[1:-1])
     K = np.block([[nu * M2psi.astype(complex), Cpc], [Ccp, (vs * Dc + kappa * Mc).astype(complex)]])
     W = np.block([[Mpsi.astype(complex), np.zeros((n, nc))], [np.zeros((nc, n)), np.eye(nc)]])
+    sig = linalg.eigvals(K, W)
+    sig = sig[np.isfinite(sig)]
+    return float(np.max(sig.real))
+
+
+def growth_rate_sugar(k, H, nu, A, kappa, vs, cbar_fn, gS=0.0, Ds=0.0, Sbar_fn=None, phi0=0.0, m=400):
+    """Largest real part of sigma(k) with the sugar scalar (Sec. 3.2, the full x = (psi, omega,
+    S, phi) problem with omega eliminated), in the lattice form of the model:
+        F_y = -A c - gS S (1 - phi0 c)                     (A = g R, gS = g S*)
+        sigma M psi = nu M^2 psi + i k [(A - gS phi0 Sbar) c + gS (1 - phi0 cbar) S]
+        sigma c     = i k cbar' psi + (Vs D + kappa M) c
+        sigma S     = i k Sbar' psi + Ds M S
+    x = (psi, c, S); clamped psi, Neumann c and S, as in ``growth_rate``.  Vs is constant in
+    the linearisation (the paper drops the -phi div(Vs e_z) term, Sec. 3.1)."""
+    h = H / m
+    y = np.linspace(0.0, H, m + 1)
+    n = m - 1
+    D2 = (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)) / h**2
+    D4 = (np.diag(6.0 * np.ones(n)) + np.diag(-4.0 * np.ones(n - 1), 1) + np.diag(-4.0 * np.ones(n - 1), -1)
+          + np.diag(np.ones(n - 2), 2) + np.diag(np.ones(n - 2), -2))
+    D4[0, 0] += 1.0
+    D4[-1, -1] += 1.0
+    D4 /= h**4
+    I = np.eye(n)
+    Mpsi = D2 - k**2 * I
+    M2psi = D4 - 2.0 * k**2 * D2 + k**4 * I
+    nc = m + 1
+    Dc = np.zeros((nc, nc))
+    D2c = np.zeros((nc, nc))
+    for j in range(nc):
+        jm, jp = j - 1, j + 1
+        if jm < 0:
+            jm = 1
+        if jp > m:
+            jp = m - 1
+        if 0 < j < m:
+            Dc[j, jp] += 0.5 / h
+            Dc[j, jm] -= 0.5 / h
+        D2c[j, jp] += 1.0 / h**2
+        D2c[j, jm] += 1.0 / h**2
+        D2c[j, j] -= 2.0 / h**2
+    Mc = D2c - k**2 * np.eye(nc)
+    cb = cbar_fn(y)
+    Sb = Sbar_fn(y) if Sbar_fn is not None else np.zeros_like(y)
+    dcb = np.gradient(cb, y)
+    dSb = np.gradient(Sb, y)
+    Aeff = A - gS * phi0 * Sb        # coefficient of c in -F_y
+    Beff = gS * (1.0 - phi0 * cb)    # coefficient of S in -F_y
+    Cpc = np.zeros((n, nc), dtype=complex)
+    Cpc[:, 1:-1] = 1j * k * np.diag(Aeff[1:-1])
+    CpS = np.zeros((n, nc), dtype=complex)
+    CpS[:, 1:-1] = 1j * k * np.diag(Beff[1:-1])
+    Ccp = np.zeros((nc, n), dtype=complex)
+    Ccp[1:-1, :] = 1j * k * np.diag(dcb[1:-1])
+    CSp = np.zeros((nc, n), dtype=complex)
+    CSp[1:-1, :] = 1j * k * np.diag(dSb[1:-1])
+    Z = np.zeros((nc, nc))
+    K = np.block([[nu * M2psi.astype(complex), Cpc, CpS],
+                  [Ccp, (vs * Dc + kappa * Mc).astype(complex), Z],
+                  [CSp, Z, (Ds * Mc).astype(complex)]])
+    W = np.block([[Mpsi.astype(complex), np.zeros((n, nc)), np.zeros((n, nc))],
+                  [np.zeros((nc, n)), np.eye(nc), Z],
+                  [np.zeros((nc, n)), Z, np.eye(nc)]])
     sig = linalg.eigvals(K, W)
     sig = sig[np.isfinite(sig)]
     return float(np.max(sig.real))

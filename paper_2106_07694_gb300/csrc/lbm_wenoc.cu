@@ -241,6 +241,18 @@ void launch(lbm_wenoc* h, int kind, F&& f) {
 template <class LAT, typename T>
 void enqueue_transport(lbm_wenoc* h, const Args<T>& a);
 
+// Sugar: S^{n+1} from S^n and u^n into the other buffer (after the transport of c, which
+// reads S^n).
+template <class LAT, typename T>
+void enqueue_sugar(lbm_wenoc* h, const Args<T>& a) {
+  if (!h->sugar) return;
+  const dim3 blk(kLbmThreads);
+  const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
+  cudaStream_t s = h->stream;
+  launch(h, K_SUGAR, [&] { lw::sugar_kernel<T, LAT::DIM><<<grd, blk, 0, s>>>(a); });
+  h->cur ^= 1;
+}
+
 template <class LAT, typename T>
 void enqueue_step(lbm_wenoc* h, int parity) {
   Args<T> a = make_args<T>(h);
@@ -292,6 +304,7 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
     launch(h, K_STAGE1, [&] { lw::launch_stage2d<1>(af, af.c, af.c1, H, s); });
     launch(h, K_STAGE2, [&] { lw::launch_stage2d<2>(af, af.c1, af.c2, H, s); });
     launch(h, K_STAGE3, [&] { lw::launch_stage2d<3>(af, af.c2, af.c, H, s); });  // + deposit
+    enqueue_sugar<LAT, T>(h, a);
     return;
   }
   if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d) {
@@ -312,10 +325,7 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
       lw::deposit_kernel<T><<<dep_blocks, lw::kReduceThreads, 0, s>>>(a, nfloor);
     });
   launch(h, K_STAGE3, [&] { lw::rk_stage_kernel<T, LAT::DIM, 3><<<grd, blk, 0, s>>>(a); });
-  if (h->sugar) {  // S^{n+1} from S^n and u^n into the other buffer
-    launch(h, K_SUGAR, [&] { lw::sugar_kernel<T, LAT::DIM><<<grd, blk, 0, s>>>(a); });
-    h->cur ^= 1;
-  }
+  enqueue_sugar<LAT, T>(h, a);
 }
 
 void enqueue_one(lbm_wenoc* h, int parity) {
@@ -365,7 +375,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
 
 int launches_per_step(const lbm_wenoc* h) {
   if (h->sweep) return h->frozen ? 1 : 2;
-  if (h->stage2d) return (h->frozen ? 0 : 1) + 3;
+  if (h->stage2d) return (h->frozen ? 0 : 1) + 3 + (h->sugar ? 1 : 0);
   return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0) + (h->sugar ? 1 : 0);
 }
 
@@ -451,7 +461,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   cudaGetDevice(&h->device);
   h->sweep = !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
-  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep && !h->sugar &&
+  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
                (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
   if (h->stage2d) {
     int sms = 0;

@@ -38,7 +38,7 @@ struct Stage2dParams {
 
 // Body of the stage kernel for strip bx, segment by; `strips` = number of strips (the
 // floor CTAs that fold the deposit).
-template <int STAGE>
+template <int STAGE, bool SUGAR = false>
 __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2dParams& sp, int bx, int by,
                                              int strips) {
   __shared__ __align__(16) Stage2dSmem S;
@@ -77,7 +77,9 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     const unsigned k = (unsigned)lr * (unsigned)nx + X;
     qc = __ldg(cin + k);
     const float u = __ldg(uy + k);
-    qw = fmaf(ghost ? -u : u, inv_alpha, -vs_a);
+    // with sugar the settling velocity of the node (a ghost reads its mirror's) is Vs (1 - ks S)
+    const float vsa = SUGAR ? vs_a * fmaf(-a.ks, __ldg(a.S + k), 1.f) : vs_a;
+    qw = fmaf(ghost ? -u : u, inv_alpha, -vsa);
   };
   auto col_put = [&](int l) {
     const float h = 0.5f * qc;
@@ -144,7 +146,8 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
 
     // ---- divergence and the Shu-Osher combination of this stage
     if (!prime) {
-      const float fdn = k == 0 ? -a.vs * chere : carry;
+      const float vs_floor = SUGAR && k == 0 ? a.vs * fmaf(-a.ks, __ldg(a.S + X), 1.f) : a.vs;
+      const float fdn = k == 0 ? -vs_floor * chere : carry;
       const float L = S.fx[t] - S.fx[t + 1] + fdn - fup;
       if (out) {
         float v;
@@ -159,8 +162,10 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
         sp.cout[(unsigned)k * (unsigned)nx + X] = v;
         if (STAGE == 3) {
           report_status(a.status, !isfinite(v));
-          if (k == 0)  // RK3 b-weights of the floor flux: c^n/6 + c1/6 + 2 c2/3
+          if (k == 0) {  // RK3 b-weights of the floor flux: c^n/6 + c1/6 + 2 c2/3
             dep = ((double)cn_here + (double)a.c1[X]) * (1.0 / 6.0) + (double)chere * (2.0 / 3.0);
+            if (SUGAR) dep *= (double)vs_floor;  // Vs(S) per floor node, no common factor
+          }
         }
       }
     }
@@ -180,7 +185,7 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     if (t == 0) {
       double s2 = 0.0;
       for (int w = 0; w < kS2T / 32; ++w) s2 += red[w];
-      a.partials[bx] = s2 * (double)a.vs;
+      a.partials[bx] = SUGAR ? s2 : s2 * (double)a.vs;
       __threadfence();
       last = atomicAdd(a.ticket, 1u) == (unsigned)strips - 1;
     }
@@ -196,9 +201,9 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
   }
 }
 
-template <int STAGE>
+template <int STAGE, bool SUGAR = false>
 __global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2dParams sp) {
-  stage2d_body<STAGE>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
+  stage2d_body<STAGE, SUGAR>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
@@ -220,7 +225,10 @@ inline cudaError_t launch_stage2d(const Args<float>& a, const float* cin, float*
   sp.cout = cout;
   sp.H = H;
   const dim3 grid((a.nx + kS2T - 1) / kS2T, (a.ny + H - 1) / H);
-  rk_stage2d_kernel<STAGE><<<grid, kS2T, 0, s>>>(a, sp);
+  if (a.S)
+    rk_stage2d_kernel<STAGE, true><<<grid, kS2T, 0, s>>>(a, sp);
+  else
+    rk_stage2d_kernel<STAGE><<<grid, kS2T, 0, s>>>(a, sp);
   return cudaGetLastError();
 }
 

@@ -70,7 +70,17 @@ class Workload:
         return int(np.prod(self.shape))
 
     def initial_c(self) -> np.ndarray:
-        return interface_field(self.shape, seed=self.seed)
+        return interface_field(self.shape, interface_frac=self.extra.get("interface_frac", 0.75), seed=self.seed)
+
+    def initial_S(self) -> np.ndarray:
+        """Sugar layer (S = 1) below the interface, S = 0 above, no noise (Eqs. ini1, ini)."""
+        return 1.0 - interface_field(self.shape, interface_frac=self.extra.get("interface_frac", 0.75),
+                                     amplitude=0.0, seed=self.seed)
+
+    @property
+    def sugar(self) -> dict:
+        """Keyword parameters of the sugar scalar ({} when the workload has none)."""
+        return dict(self.extra.get("sugar", {}))
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -87,6 +97,18 @@ MAIN_3D = Workload("d3q19_256x256x512_f32", (256, 256, 512), "f32", 10000, gravi
 # every 100 steps; Lax-Friedrichs alpha fixed at Vs + 0.1 (the default u_cap).
 ADJOINT_2D = Workload("d2q9_512x1024_f32_adjoint", (512, 1024), "f32", 2000,
                       extra=dict(segment=100, lf_alpha=1e-3 + 0.1))
+
+# The paper's two-layer state (Eqs. ini1, ini) on the 2048 x 4096 lattice: particles over a
+# sugar solution, statically stable.  Physical values mapped to lattice units: particle
+# contrast R = rho_p/rho_0 - 1 = 1.519 (glass beads), phi0 = 1.19e-3 (3 g/l, Table 1), with
+# g R phi0 = 1e-5 as in the plain workload (g = 5.53e-3, density_contrast = R phi0); sugar
+# S* = 0.0084 (rho_f = 1008.4 kg/m3), so the sugar layer outweighs the particles 4.6x;
+# Vs(S) = Vs (1 - S*/R S) from Eq. stokes_vel; D_s = nu / 2000 (sugar in water).
+SUGAR_2D = Workload("d2q9_2048x4096_f32_sugar", (2048, 4096), "f32", 20000, gravity=5.53e-3,
+                    density_contrast=1.808e-3,
+                    extra=dict(interface_frac=0.5,
+                               sugar=dict(sugar=True, sugar_contrast=8.4e-3, sugar_diffusivity=1.7e-5,
+                                          phi0=1.19e-3, vs_sugar=5.53e-3)))
 
 # Sweep grid of the 2048 x 4096 case: buoyancy amplitude x settling velocity.
 MAIN_2D_SWEEP = [(a, vs) for a in (1e-5, 2e-5, 5e-5) for vs in (5e-4, 1e-3, 2e-3)]

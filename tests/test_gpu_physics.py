@@ -39,3 +39,26 @@ def test_gpu_fp32_growth_rate_matches_lsa(mode):
     sigma_lsa = lsa.growth_rate(2 * np.pi * mode / nx, ny, nu, PHYS_LSA["gravity"], PHYS_LSA["diffusivity"],
                                 PHYS_LSA["settling_velocity"], lambda yy: lsa.erf_profile(yy, yc, delta), m=256)
     assert abs(sigma_sim - sigma_lsa) < 0.10 * sigma_lsa, (sigma_sim, sigma_lsa)
+
+
+def test_gpu_fp32_growth_rate_with_sugar_matches_lsa():
+    from paper_2106_07694_gb300.lbm_wenoc import Simulation
+    from tests.test_physics_lsa import SUGAR_LSA, sugar_layer, sugar_lsa_rate
+    nx, ny, mode = 64, 128, 1
+    c0 = seeded_interface(nx, ny, mode)
+    S0 = sugar_layer(nx, ny)
+    g = Simulation((nx, ny), fp64=False, u_cap=0.5, **SUGAR_LSA)
+    g.init(c0)
+    g.set_sugar(S0)
+
+    def at(t):
+        g.step(t - g.steps)
+        return g.steps, g.fields()[2].double().numpy()
+    sigma_sim = mode_growth(at, 50, 40, nx, mode)
+    h = Simulation((nx, ny), fp64=False, u_cap=0.5, **SUGAR_LSA)
+    h.init(c0)
+    h.set_sugar(S0)
+    h.step(300)
+    sigma_lsa = sugar_lsa_rate(h.fields()[2].double().numpy().mean(axis=1), h.sugar().double().numpy().mean(axis=1),
+                               ny, nx, mode, SUGAR_LSA)
+    assert abs(sigma_sim - sigma_lsa) < 0.10 * sigma_lsa, (sigma_sim, sigma_lsa)

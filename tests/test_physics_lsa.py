@@ -1,4 +1,5 @@
-"""Coupled early-time growth against linear stability analysis (Sec. 3, Sec. 4.1).
+"""Coupled early-time growth against linear stability analysis (Sec. 3, Sec. 4.1), without
+and with the sugar scalar.
 
 The paper validates its solver by comparing the early growth of the interface with the
 dispersion relation of its LSA.  Here the LSA is the K/W eigenproblem with the density-
@@ -80,4 +81,80 @@ def test_oracle_growth_rate_matches_lsa_within_10_percent():
     nu = (PHYS_LSA["tau"] - 0.5) / 3.0
     sigma_lsa = lsa.growth_rate(2 * np.pi * mode / nx, ny, nu, PHYS_LSA["gravity"], PHYS_LSA["diffusivity"],
                                 PHYS_LSA["settling_velocity"], lambda yy: lsa.erf_profile(yy, yc, delta), m=256)
+    assert abs(sigma_sim - sigma_lsa) < 0.10 * sigma_lsa, (sigma_sim, sigma_lsa)
+
+
+# ---- with the sugar scalar (the paper's full K/W problem) --------------------------------
+
+def test_lsa_sugar_reductions():
+    k, H, nu = 2 * np.pi / 64, 128.0, 1 / 30
+    cb = lambda y: lsa.erf_profile(y, 64.0, 3.0)
+    zero = lambda y: np.zeros_like(y)
+    # S* = 0: the one-scalar problem
+    a = lsa.growth_rate(k, H, nu, 1e-3, 1e-3, 1e-3, cb, m=128)
+    b = lsa.growth_rate_sugar(k, H, nu, 1e-3, 1e-3, 1e-3, cb, m=128)
+    assert b == pytest.approx(a, rel=1e-10)
+    # sugar alone, heavy on top: the one-scalar problem with A -> g S*, kappa -> D_s, Vs -> 0
+    Sb = lambda y: lsa.erf_profile(y, 64.0, 3.0)
+    s1 = lsa.growth_rate_sugar(k, H, nu, 0.0, 1e-3, 0.0, zero, gS=2e-3, Ds=5e-4, Sbar_fn=Sb, m=128)
+    s2 = lsa.growth_rate(k, H, nu, 2e-3, 5e-4, 0.0, Sb, m=128)
+    assert s1 == pytest.approx(s2, rel=1e-10) and s1 > 0
+    # sugar alone, heavy below: statically stable, nothing grows
+    stable = lsa.growth_rate_sugar(k, H, nu, 0.0, 1e-3, 0.0, zero, gS=2e-3, Ds=5e-4,
+                                   Sbar_fn=lambda y: 1 - Sb(y), m=128)
+    assert stable <= 1e-12
+
+
+def test_lsa_sugar_layer_below_slows_then_stops_the_growth():
+    k, H, nu = 2 * np.pi / 64, 128.0, 1 / 30
+    cb = lambda y: lsa.erf_profile(y, 64.0, 3.0)
+    Sb = lambda y: 1 - lsa.erf_profile(y, 64.0, 3.0)
+    rates = [lsa.growth_rate_sugar(k, H, nu, 1e-3, 1e-3, 1e-3, cb, gS=g, Ds=5e-4, Sbar_fn=Sb, phi0=0.01, m=128)
+             for g in (0.0, 0.5e-3, 1e-3, 2e-3)]
+    assert rates[0] > rates[1] > rates[2] > 0 >= rates[3]
+
+
+SUGAR_LSA = dict(PHYS_LSA, sugar=True, sugar_contrast=0.5, sugar_diffusivity=1e-3, phi0=0.0, vs_sugar=0.0)
+
+
+def sugar_layer(nx, ny):
+    """Sugar (S = 1) below the interface of seeded_interface, S = 0 above."""
+    y = np.arange(ny)[:, None] + 0.5
+    return 0.5 * (1.0 - np.tanh((y - 0.5 * ny) / 2.0)) * np.ones((1, nx))
+
+
+def sugar_lsa_rate(c_mean, S_mean, ny, nx, mode, kw):
+    y = np.arange(ny) + 0.5
+    yc, delta = lsa.fit_erf(y, c_mean)
+    ys, ds = lsa.fit_erf(y, 1.0 - S_mean)
+    nu = (kw["tau"] - 0.5) / 3.0
+    return lsa.growth_rate_sugar(2 * np.pi * mode / nx, ny, nu, kw["gravity"] * kw["density_contrast"],
+                                 kw["diffusivity"], kw["settling_velocity"], lambda yy: lsa.erf_profile(yy, yc, delta),
+                                 gS=kw["gravity"] * kw["sugar_contrast"], Ds=kw["sugar_diffusivity"],
+                                 Sbar_fn=lambda yy: 1.0 - lsa.erf_profile(yy, ys, ds), phi0=kw["phi0"], m=256)
+
+
+@pytest.mark.slow
+def test_oracle_growth_rate_with_sugar_matches_lsa_within_10_percent():
+    # particles over a lighter-than-them sugar layer (S* g = A/2): still unstable, slower
+    nx, ny, mode = 64, 128, 1
+    c0 = seeded_interface(nx, ny, mode)
+    S0 = sugar_layer(nx, ny)
+    s = oracle.OracleSim((nx, ny), u_cap=0.5, **SUGAR_LSA)
+    s.init(c0)
+    s.set_sugar(S0)
+
+    def at(t):
+        s.step(t - s.steps)
+        return s.steps, s.fields()[2]
+    sigma_sim = mode_growth(at, 50, 40, nx, mode)
+    s2 = oracle.OracleSim((nx, ny), u_cap=0.5, **SUGAR_LSA)
+    s2.init(c0)
+    s2.set_sugar(S0)
+    s2.step(300)
+    sigma_lsa = sugar_lsa_rate(s2.fields()[2].mean(axis=1), s2.sugar().mean(axis=1), ny, nx, mode, SUGAR_LSA)
+    no_sugar = lsa.growth_rate(2 * np.pi * mode / nx, ny, (PHYS_LSA["tau"] - 0.5) / 3.0, PHYS_LSA["gravity"],
+                               PHYS_LSA["diffusivity"], PHYS_LSA["settling_velocity"],
+                               lambda yy: lsa.erf_profile(yy, 57.0, 3.0), m=256)
+    assert sigma_lsa < 0.85 * no_sugar  # the sugar term matters at this contrast
     assert abs(sigma_sim - sigma_lsa) < 0.10 * sigma_lsa, (sigma_sim, sigma_lsa)
