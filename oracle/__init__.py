@@ -19,6 +19,8 @@ from . import build as _build
 ORC_PERIODIC_VERTICAL = 1
 ORC_FROZEN_VELOCITY = 2
 ORC_SUGAR = 4
+ORC_WENO3 = 8
+ORC_SIGN_SPLIT = 16
 
 
 class _Params(ctypes.Structure):
@@ -72,6 +74,8 @@ def lib():
         L.orc_transport_rate.argtypes = [ctypes.c_void_p, dp, dp, dp]
         L.orc_weno5_left.argtypes = [dp, ctypes.c_double]
         L.orc_weno5_left.restype = ctypes.c_double
+        L.orc_weno3_left.argtypes = [dp, ctypes.c_double]
+        L.orc_weno3_left.restype = ctypes.c_double
         L.orc_lattice.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), dp]
         L.orc_lattice.restype = ctypes.c_int
         L.orc_deposit_gradient.argtypes = [ctypes.POINTER(_Params), dp, ctypes.c_int64, dp, dp, dp]
@@ -96,7 +100,8 @@ def weno5_left(v, eps):
 
 def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0, diffusivity=0.0,
             lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False,
-            sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0):
+            sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0, weno3=False,
+            sign_split=False):
     p = _Params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -107,7 +112,8 @@ def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity
     for d in range(3):
         p.body_force[d] = float(body_force[d]) if d < len(body_force) else 0.0
     p.flags = (ORC_PERIODIC_VERTICAL if periodic_vertical else 0) | \
-              (ORC_FROZEN_VELOCITY if frozen_velocity else 0) | (ORC_SUGAR if sugar else 0)
+              (ORC_FROZEN_VELOCITY if frozen_velocity else 0) | (ORC_SUGAR if sugar else 0) | \
+              (ORC_WENO3 if weno3 else 0) | (ORC_SIGN_SPLIT if sign_split else 0)
     p.sugar_contrast, p.sugar_diffusivity, p.phi0, p.vs_sugar = sugar_contrast, sugar_diffusivity, phi0, vs_sugar
     return p
 
@@ -128,6 +134,13 @@ def deposit_gradient(shape, c0, nsteps, **params):
     return J.value, g, dvs.value
 
 
+def weno3_left(v, eps):
+    """One third-order WENO face value from the upwind-side values v[0..2] = h_{i-1..i+1}."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.shape == (3,)
+    return lib().orc_weno3_left(_dptr(v), float(eps))
+
+
 class OracleSim:
     """A simulation held by the C oracle.
 
@@ -138,11 +151,12 @@ class OracleSim:
     def __init__(self, shape, tau=0.6, gravity=0.0, density_contrast=1.0,
                  settling_velocity=0.0, diffusivity=0.0, lf_alpha=0.0, u_cap=0.0,
                  body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False,
-                 sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0):
+                 sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0, weno3=False,
+                 sign_split=False):
         dim = len(shape)
         p = _params(shape, tau, gravity, density_contrast, settling_velocity, diffusivity, lf_alpha, u_cap,
                     body_force, periodic_vertical, frozen_velocity, sugar, sugar_contrast, sugar_diffusivity,
-                    phi0, vs_sugar)
+                    phi0, vs_sugar, weno3, sign_split)
         self._p = p
         self.dim = dim
         self.grid = tuple(reversed([int(s) for s in shape]))  # numpy shape, vertical first

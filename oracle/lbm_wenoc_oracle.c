@@ -23,6 +23,11 @@
  * With ORC_SUGAR, a second scalar S (sugar, normalised by its lower-layer value S0):
  *   s1  force F_v = -g [R c + S* S (1 - phi0 c)]                   (Eq. forceterm; rho/rho0 - 1 = S* S)
  *   s2  settling velocity Vs (1 - kS S) in every face velocity     (Eq. stokes_vel with rho(S))
+ * Variants of a4/a5: ORC_WENO3, the paper's third-order WENO with two two-point stencils
+ * (Supplement Eqs. S10, S11, S14-S16 for the left-biased side, S17-S20 as its mirror
+ * image), linear weights (2/3, 1/3) of Eq. S16; ORC_SIGN_SPLIT, the whole flux w c
+ * reconstructed from the upwind side chosen by the sign of the face velocity
+ * (w_i + w_{i+1})/2 (ties: left-biased), the paper's "upwind splitting of the flux".
  *   s3  S advanced by first-order upwind in advective form, one    (Eq. AD; Supplement Eqs. S5, S6)
  *       explicit step per axis sign, plus central diffusion D_s,
  *       with the velocity of a1 and Neumann walls (Eq. neum2)
@@ -46,6 +51,8 @@
 #define ORC_PERIODIC_VERTICAL 1u /* vertical axis periodic too: no walls, no deposit */
 #define ORC_FROZEN_VELOCITY 2u   /* fluid not advanced; transport uses the velocity given at init */
 #define ORC_SUGAR 4u             /* second scalar S (sugar) in the force, Vs and its own transport */
+#define ORC_WENO3 8u             /* the paper's third-order WENO (Supplement Eqs. S10-S20) instead of WENO5 */
+#define ORC_SIGN_SPLIT 16u       /* split by the sign of the face velocity instead of Lax-Friedrichs */
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -266,6 +273,25 @@ double orc_weno5_left(const double v[5], double eps) {
   return h;
 }
 
+/* ---- a5 variant: one third-order WENO reconstruction, upwind side on the left ----
+ * v[0..2] are the flux values at i-1, i, i+1; the result approximates the flux at the
+ * face i+1/2: candidates h1 = (h_i + h_{i+1})/2 (S10) and h2 = -(h_{i-1} - 3 h_i)/2 (S11),
+ * smoothness indicators beta1 = (h_{i+1} - h_i)^2, beta2 = (h_i - h_{i-1})^2 and weights
+ * alpha_j/(eps + beta_j)^2 with alpha = (2/3, 1/3), normalised (S14-S16).  For the other
+ * side the caller passes the mirror image (S17-S20). */
+double orc_weno3_left(const double v[3], double eps) {
+  const double hm1 = v[0], h0 = v[1], hp1 = v[2];
+  const double q[2] = {0.5 * (h0 + hp1), -0.5 * (hm1 - 3.0 * h0)};
+  const double beta[2] = {(hp1 - h0) * (hp1 - h0), (h0 - hm1) * (h0 - hm1)};
+  const double lin[2] = {2.0 / 3.0, 1.0 / 3.0};
+  double wt[2], sum = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    wt[k] = lin[k] / ((eps + beta[k]) * (eps + beta[k]));
+    sum += wt[k];
+  }
+  return wt[0] / sum * q[0] + wt[1] / sum * q[1];
+}
+
 /* Vertical ghost handling: index reflected into the fluid and whether it was a ghost. */
 static int reflect_vertical(int v, int n, int *ghost) {
   *ghost = 0;
@@ -286,7 +312,7 @@ static double face_flux(const orc_sim *s, const double *c, int xyz[3], int d) {
   const size_t nn = s->nn;
   const int va = s->vaxis;
   const int walls = vertical_walls(s) && d == va;
-  double hp[6], hm[6], cv[6];
+  double hp[6], hm[6], cv[6], wv[6];
   for (int m = -2; m <= 3; ++m) {
     int p[3] = {xyz[0], xyz[1], xyz[2]};
     int ghost = 0;
@@ -300,16 +326,35 @@ static double face_flux(const orc_sim *s, const double *c, int xyz[3], int d) {
     if (ghost) ud = -ud; /* no-slip wall: velocity odd about the wall */
     double w = ud - (d == va ? settling_at(s, k) : 0.0);
     cv[m + 2] = cval;
+    wv[m + 2] = w;
     hp[m + 2] = 0.5 * (w + s->alpha) * cval;
     hm[m + 2] = 0.5 * (w - s->alpha) * cval;
+  }
+  /* a6: central diffusion, flux = -kappa dc/dx at the face */
+  const double fdiff = -s->p.diffusivity * (cv[3] - cv[2]);
+  const int weno3 = (s->p.flags & ORC_WENO3) != 0;
+  if (s->p.flags & ORC_SIGN_SPLIT) {
+    /* whole flux h = w c, from the side the face velocity (w_i + w_{i+1})/2 comes from */
+    double h[6];
+    for (int m = 0; m < 6; ++m) h[m] = wv[m] * cv[m];
+    const int from_left = 0.5 * (wv[2] + wv[3]) >= 0.0;
+    if (weno3) {
+      const double left[3] = {h[1], h[2], h[3]}, right[3] = {h[4], h[3], h[2]};
+      return orc_weno3_left(from_left ? left : right, s->eps) + fdiff;
+    }
+    const double left[5] = {h[0], h[1], h[2], h[3], h[4]}, right[5] = {h[5], h[4], h[3], h[2], h[1]};
+    return orc_weno5_left(from_left ? left : right, s->eps) + fdiff;
+  }
+  if (weno3) {
+    /* h+ : points i-1..i+1; h- : mirror image, points i+2..i */
+    const double left[3] = {hp[1], hp[2], hp[3]}, right[3] = {hm[4], hm[3], hm[2]};
+    return orc_weno3_left(left, s->eps) + orc_weno3_left(right, s->eps) + fdiff;
   }
   /* h+ : upwind from the left, points i-2..i+2 */
   double fplus = orc_weno5_left(hp, s->eps);
   /* h- : mirror image, points i+3..i-1 read right to left */
   const double mirror[5] = {hm[5], hm[4], hm[3], hm[2], hm[1]};
   double fminus = orc_weno5_left(mirror, s->eps);
-  /* a6: central diffusion, flux = -kappa dc/dx at the face */
-  double fdiff = -s->p.diffusivity * (cv[3] - cv[2]);
   return fplus + fminus + fdiff;
 }
 
@@ -840,7 +885,8 @@ static void fluid_adjoint(orc_sim *s, const double *f, const double *c, const do
 int orc_deposit_gradient(const orc_params *p, const double *c0, int64_t nsteps, double *grad_c0, double *dJ_dVs,
                          double *J) {
   if (!p || !c0 || !grad_c0 || !dJ_dVs || !J || nsteps < 1) return ORC_EINVAL;
-  if (p->dim != 2 || (p->flags & (ORC_PERIODIC_VERTICAL | ORC_FROZEN_VELOCITY | ORC_SUGAR)) ||
+  if (p->dim != 2 ||
+      (p->flags & (ORC_PERIODIC_VERTICAL | ORC_FROZEN_VELOCITY | ORC_SUGAR | ORC_WENO3 | ORC_SIGN_SPLIT)) ||
       !(p->lf_alpha > 0.0))
     return ORC_EINVAL;
   orc_sim *s = orc_create(p);
