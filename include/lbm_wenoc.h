@@ -55,6 +55,12 @@ extern "C" {
                                      force -g S* S (1 - phi0 c), settling velocity Vs (1 - kS S), S
                                      advected by first-order upwind (Supplement Eqs. S5, S6) with
                                      diffusion D_s; not with LW_FUSED_RK3, batches or the gradient */
+#define LW_WENO3 0x40u            /* the paper's third-order WENO (Supplement Eqs. S10-S20, linear weights
+                                     (2/3, 1/3) of Eq. S16) instead of WENO5; generic stage kernels */
+#define LW_SIGN_SPLIT 0x80u       /* whole flux w c reconstructed from the side the face velocity
+                                     (w_i + w_{i+1})/2 comes from (ties left) instead of the
+                                     Lax-Friedrichs split; generic stage kernels.  Neither variant with
+                                     LW_FUSED_RK3, batches or the gradient */
 
 typedef struct lbm_wenoc lbm_wenoc; /* opaque host-side handle */
 
@@ -70,7 +76,7 @@ typedef struct {
   double u_cap;              /* bound on |u_d| checked on the device; 0 selects 0.1 */
   double body_force[3];      /* extra uniform force (e.g. a channel flow), added to the buoyancy */
   uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH | LW_FUSED_RK3
-                                | LW_SUGAR */
+                                | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT */
   /* used with LW_SUGAR only (S normalised by its lower-layer value S0) */
   double sugar_contrast;     /* S* = rho(S0)/rho_0 - 1 (Eq. S_star): force -gravity*S* S (1 - phi0 c) e_v */
   double sugar_diffusivity;  /* D_s >= 0 */

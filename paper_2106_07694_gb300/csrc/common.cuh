@@ -39,7 +39,11 @@ struct Args {
   T phi0;      // particle volume fraction at c = 1
   T ks;        // settling velocity Vs (1 - ks S)
   T Ds;        // sugar diffusivity
+  int scheme;  // flux variant bits (kSchemeWeno3, kSchemeSignSplit); 0 = WENO5, Lax-Friedrichs
 };
+
+constexpr int kSchemeWeno3 = 1;
+constexpr int kSchemeSignSplit = 2;
 
 // Settling velocity at node m: Vs, or Vs (1 - ks S_m) with sugar.
 template <typename T>

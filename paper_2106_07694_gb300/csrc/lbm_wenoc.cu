@@ -92,6 +92,7 @@ int check_params(const lbm_wenoc_params* p) {
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LW_EINVAL;  // stability needs tau > 1/2
   if (!(p->settling_velocity >= 0.0) || !(p->diffusivity >= 0.0)) return LW_EINVAL;
   if (!(p->lf_alpha >= 0.0) || !(p->u_cap >= 0.0)) return LW_EINVAL;
+  if ((p->flags & (LW_WENO3 | LW_SIGN_SPLIT)) && (p->flags & LW_FUSED_RK3)) return LW_EINVAL;
   if ((p->flags & LW_SUGAR) && ((p->flags & LW_FUSED_RK3) || !(p->sugar_diffusivity >= 0.0) ||
                                 !std::isfinite(p->sugar_contrast) || !std::isfinite(p->phi0) ||
                                 !std::isfinite(p->vs_sugar)))
@@ -172,6 +173,7 @@ Args<T> make_args(const lbm_wenoc* h) {
   a.alpha = T(h->alpha);
   a.inv_alpha = T(1.0 / h->alpha);
   a.u_cap = T(p.u_cap);
+  a.scheme = ((p.flags & LW_WENO3) ? lw::kSchemeWeno3 : 0) | ((p.flags & LW_SIGN_SPLIT) ? lw::kSchemeSignSplit : 0);
   if (h->sugar) {
     a.S = reinterpret_cast<T*>(b + (h->cur ? h->L.sb : h->L.sa));
     a.S2 = reinterpret_cast<T*>(b + (h->cur ? h->L.sa : h->L.sb));
@@ -455,13 +457,14 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   h->walls = (p->flags & LW_PERIODIC_VERTICAL) == 0;
   h->frozen = (p->flags & LW_FROZEN_VELOCITY) != 0;
   h->sugar = (p->flags & LW_SUGAR) != 0;
+  const bool variant = (p->flags & (LW_WENO3 | LW_SIGN_SPLIT)) != 0;  // generic stage kernels
   h->use_graphs = (p->flags & LW_NO_GRAPH) == 0;
   h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : p->settling_velocity + h->p.u_cap;
   cudaGetDevice(&h->device);
-  h->sweep = !h->fp64 && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
+  h->sweep = !h->fp64 && !variant && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
-  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
+  h->stage2d = !h->fp64 && !variant && h->p.dim == 2 && h->walls && !h->sweep &&
                (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
   if (h->stage2d) {
     int sms = 0;
@@ -478,7 +481,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
       return LW_ECUDA;
     }
   }
-  h->sweep3d = !h->fp64 && h->p.dim == 3 && !h->sugar && lw::sweep3d_supported(h->p.nz, h->walls);
+  h->sweep3d = !h->fp64 && !variant && h->p.dim == 3 && !h->sugar && lw::sweep3d_supported(h->p.nz, h->walls);
   if (h->sweep3d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
@@ -762,7 +765,7 @@ namespace {
 
 bool batch_params_ok(const lbm_wenoc_params& p) {
   return check_params(&p) == LW_OK && p.dim == 2 && !(p.flags & LW_FP64) && !(p.flags & LW_PERIODIC_VERTICAL) &&
-         !(p.flags & LW_FROZEN_VELOCITY) && !(p.flags & LW_FUSED_RK3) && !(p.flags & LW_SUGAR) &&
+         !(p.flags & (LW_FROZEN_VELOCITY | LW_FUSED_RK3 | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT)) &&
          (p.nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
 }
 
@@ -1014,7 +1017,8 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
 namespace {
 
 bool gradient_params_ok(const lbm_wenoc* h) {
-  return h && h->p.dim == 2 && h->walls && !h->frozen && !h->sweep && !h->sugar && h->p.lf_alpha > 0.0;
+  return h && h->p.dim == 2 && h->walls && !h->frozen && !h->sweep && !h->sugar &&
+         !(h->p.flags & (LW_WENO3 | LW_SIGN_SPLIT)) && h->p.lf_alpha > 0.0;
 }
 
 struct GradLayout {

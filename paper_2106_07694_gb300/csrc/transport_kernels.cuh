@@ -14,8 +14,13 @@
 //       a wall read ghosts (c even, fluid velocity odd, Vs unchanged); the lid face
 //       carries no flux; the floor face carries the settling outflow -Vs c_0.
 //
-// This file holds the generic one-node-per-thread form used for every lattice and
-// precision; the 2D FP32 production kernel lives in transport_sweep2d.cuh.
+// Variants (Args::scheme): kSchemeWeno3, the paper's third-order WENO (Supplement Eqs.
+// S10-S20) instead of WENO5; kSchemeSignSplit, the whole flux w c reconstructed from the
+// side the face velocity comes from instead of the Lax-Friedrichs split.
+//
+// This file holds the generic one-node-per-thread form used for every lattice, precision
+// and variant; the 2D/3D FP32 production kernels live in transport_stage2d.cuh,
+// transport_sweep2d.cuh and transport_sweep3d.cuh.
 #pragma once
 #include "common.cuh"
 
@@ -50,6 +55,23 @@ __device__ __forceinline__ void weno5_face(T a, T b, T c, T d, T e, T& num, T& d
   den = T(6) * (p0 + p1 + p2);
 }
 
+// The paper's third-order WENO face value (Supplement Eqs. S10, S11, S14-S16), upwind side
+// on the left: a, b, c = h_{i-1}, h_i, h_{i+1} (scaled by 1/alpha, eps as above);
+// candidates (b + c)/2 and (3b - a)/2, indicators (c - b)^2 and (b - a)^2, linear
+// weights (2/3, 1/3); one division: face value = num / den.
+template <typename T>
+__device__ __forceinline__ void weno3_face(T a, T b, T c, T& num, T& den) {
+  const T eps = T(1e-6);
+  T a1 = eps + (c - b) * (c - b);
+  T a2 = eps + (b - a) * (b - a);
+  a1 *= a1;
+  a2 *= a2;
+  const T p1 = T(2) * a2;  // (2/3)/a1 and (1/3)/a2 over the common factor 1/(3 a1 a2)
+  const T p2 = a1;
+  num = p1 * (b + c) + p2 * (T(3) * b - a);
+  den = T(2) * (p1 + p2);
+}
+
 template <typename T>
 __device__ __forceinline__ T fast_div(T x, T y) { return x / y; }
 template <>
@@ -67,7 +89,7 @@ __device__ __forceinline__ T face_flux(const Args<T>& a, const T* __restrict__ c
   const long long stride[3] = {1, a.nx, (long long)a.nx * a.ny};
   const long long base = ((long long)z * a.ny + y) * a.nx + x - (long long)pos0[d] * stride[d];
   const bool wall_axis = (d == VA) && a.walls;
-  T hp[6], hm[6], cv[6];
+  T hp[6], hm[6], cv[6], wsv[6];
 #pragma unroll
   for (int k = -2; k <= 3; ++k) {
     int p = pos0[d] + k;
@@ -90,13 +112,40 @@ __device__ __forceinline__ T face_flux(const Args<T>& a, const T* __restrict__ c
     const T sv = (d == VA) ? settling_at(a, m) : T(0);  // Vs, or Vs(S) with sugar
     const T ws = (ud - sv) * a.inv_alpha;               // w / alpha
     cv[k + 2] = cval;
+    wsv[k + 2] = ws;
     hp[k + 2] = T(0.5) * (ws + T(1)) * cval;
     hm[k + 2] = T(0.5) * (ws - T(1)) * cval;
   }
+  const T diff = a.kappa * (cv[3] - cv[2]);
+  if (a.scheme & kSchemeSignSplit) {
+    // whole flux w c from the side the face velocity (w_i + w_{i+1})/2 comes from
+    T h[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = wsv[k] * cv[k];
+    const bool left = wsv[2] + wsv[3] >= T(0);
+    T n_, d_;
+    if (a.scheme & kSchemeWeno3) {
+      if (left)
+        weno3_face<T>(h[1], h[2], h[3], n_, d_);
+      else
+        weno3_face<T>(h[4], h[3], h[2], n_, d_);
+    } else {
+      if (left)
+        weno5_face<T>(h[0], h[1], h[2], h[3], h[4], n_, d_);
+      else
+        weno5_face<T>(h[5], h[4], h[3], h[2], h[1], n_, d_);
+    }
+    return a.alpha * fast_div(n_, d_) - diff;
+  }
   T np, dp, nm, dm;
-  weno5_face<T>(hp[0], hp[1], hp[2], hp[3], hp[4], np, dp);
-  weno5_face<T>(hm[5], hm[4], hm[3], hm[2], hm[1], nm, dm);
-  return a.alpha * (fast_div(np, dp) + fast_div(nm, dm)) - a.kappa * (cv[3] - cv[2]);
+  if (a.scheme & kSchemeWeno3) {
+    weno3_face<T>(hp[1], hp[2], hp[3], np, dp);
+    weno3_face<T>(hm[4], hm[3], hm[2], nm, dm);
+  } else {
+    weno5_face<T>(hp[0], hp[1], hp[2], hp[3], hp[4], np, dp);
+    weno5_face<T>(hm[5], hm[4], hm[3], hm[2], hm[1], nm, dm);
+  }
+  return a.alpha * (fast_div(np, dp) + fast_div(nm, dm)) - diff;
 }
 
 // One RK3 stage on every node.  STAGE 1: c1 = c + L(c).  STAGE 2: c2 = 3/4 c + 1/4 c1 +
