@@ -42,6 +42,8 @@ class _Params(ctypes.Structure):
         ("sugar_diffusivity", ctypes.c_double),
         ("phi0", ctypes.c_double),
         ("vs_sugar", ctypes.c_double),
+        ("n_classes", ctypes.c_int32),
+        ("class_vs", ctypes.c_double * 8),
     ]
 
 
@@ -81,6 +83,12 @@ def lib():
         L.orc_deposit_gradient.argtypes = [ctypes.POINTER(_Params), dp, ctypes.c_int64, dp, dp, dp]
         L.orc_deposit_gradient.restype = ctypes.c_int
         L.orc_set_sugar.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_class.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+        L.orc_set_class.restype = ctypes.c_int
+        L.orc_class.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+        L.orc_class.restype = ctypes.c_int
+        L.orc_class_deposit.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_class_deposit.restype = ctypes.c_double
         L.orc_set_sugar.restype = ctypes.c_int
         L.orc_sugar.argtypes = [ctypes.c_void_p, dp]
         _lib = L
@@ -101,7 +109,7 @@ def weno5_left(v, eps):
 def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity=0.0, diffusivity=0.0,
             lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False,
             sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0, weno3=False,
-            sign_split=False):
+            sign_split=False, class_vs=()):
     p = _Params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -115,6 +123,9 @@ def _params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velocity
               (ORC_FROZEN_VELOCITY if frozen_velocity else 0) | (ORC_SUGAR if sugar else 0) | \
               (ORC_WENO3 if weno3 else 0) | (ORC_SIGN_SPLIT if sign_split else 0)
     p.sugar_contrast, p.sugar_diffusivity, p.phi0, p.vs_sugar = sugar_contrast, sugar_diffusivity, phi0, vs_sugar
+    p.n_classes = len(class_vs)
+    for k, v in enumerate(class_vs):
+        p.class_vs[k] = float(v)
     return p
 
 
@@ -152,11 +163,11 @@ class OracleSim:
                  settling_velocity=0.0, diffusivity=0.0, lf_alpha=0.0, u_cap=0.0,
                  body_force=(0.0, 0.0, 0.0), periodic_vertical=False, frozen_velocity=False,
                  sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0, weno3=False,
-                 sign_split=False):
+                 sign_split=False, class_vs=()):
         dim = len(shape)
         p = _params(shape, tau, gravity, density_contrast, settling_velocity, diffusivity, lf_alpha, u_cap,
                     body_force, periodic_vertical, frozen_velocity, sugar, sugar_contrast, sugar_diffusivity,
-                    phi0, vs_sugar, weno3, sign_split)
+                    phi0, vs_sugar, weno3, sign_split, class_vs)
         self._p = p
         self.dim = dim
         self.grid = tuple(reversed([int(s) for s in shape]))  # numpy shape, vertical first
@@ -199,6 +210,23 @@ class OracleSim:
         S = np.empty(self.grid)
         lib().orc_sugar(self._h, _dptr(S))
         return S
+
+    def set_class(self, k, ck):
+        """Particle class k (polydisperse handles), after init (class 0 = c0 there)."""
+        ck = np.ascontiguousarray(ck, dtype=np.float64).reshape(self.grid)
+        self._cls_keep = getattr(self, "_cls_keep", {})
+        self._cls_keep[k] = ck
+        if lib().orc_set_class(self._h, int(k), _dptr(ck)) != 0:
+            raise RuntimeError("orc_set_class failed")
+
+    def class_field(self, k):
+        out = np.empty(self.grid)
+        if lib().orc_class(self._h, int(k), _dptr(out)) != 0:
+            raise RuntimeError("orc_class failed")
+        return out
+
+    def class_deposit(self, k):
+        return lib().orc_class_deposit(self._h, int(k))
 
     def step(self, n=1):
         return lib().orc_step(self._h, int(n))

@@ -28,6 +28,9 @@
  * image), linear weights (2/3, 1/3) of Eq. S16; ORC_SIGN_SPLIT, the whole flux w c
  * reconstructed from the upwind side chosen by the sign of the face velocity
  * (w_i + w_{i+1})/2 (ties: left-biased), the paper's "upwind splitting of the flux".
+ * Polydisperse (n_classes >= 2, Eqs. forceterm_poly, poly): classes c_k, each transported by
+ * a4-a9 with its own settling velocity and deposit; the force (and the sugar term's
+ * (1 - phi) factor) reads phi_tot = sum_k c_k.
  *   s3  S advanced by first-order upwind in advective form, one    (Eq. AD; Supplement Eqs. S5, S6)
  *       explicit step per axis sign, plus central diffusion D_s,
  *       with the velocity of a1 and Neumann walls (Eq. neum2)
@@ -67,7 +70,7 @@ typedef struct {
   double density_contrast;
   double settling_velocity;
   double diffusivity;
-  double lf_alpha; /* 0 selects settling_velocity + u_cap */
+  double lf_alpha; /* 0 selects the (largest class) settling velocity + u_cap */
   double u_cap;    /* 0 selects 0.1 */
   double body_force[3];
   uint32_t flags;
@@ -75,6 +78,8 @@ typedef struct {
   double sugar_diffusivity; /* D_s */
   double phi0;              /* particle volume fraction at c = 1, in the (1 - phi) factor */
   double vs_sugar;          /* kS: Vs(S) = Vs (1 - kS S) */
+  int32_t n_classes;        /* >= 2: polydisperse, class k settles at class_vs[k] */
+  double class_vs[8];
 } orc_params;
 
 typedef struct {
@@ -95,6 +100,11 @@ typedef struct {
   double *rho;
   double *c1, *c2, *L, *flux;
   double *S, *Snew; /* sugar (ORC_SUGAR) */
+  int ncls;         /* particle classes (1, or n_classes) */
+  double *cls;      /* classes 1..ncls-1 (class 0 is c) */
+  double *ctot;     /* sum of the classes: the phi_tot of the force */
+  double cls_dep[8];
+  double vs_cur;    /* settling velocity of the class being transported */
   double deposit;
   int64_t steps;
   int status;
@@ -172,12 +182,26 @@ static void node_force_s(const orc_sim *s, double cval, double sval, double F[3]
 }
 
 static void node_force(const orc_sim *s, size_t k, double F[3]) {
-  node_force_s(s, s->c[k], sugar_on(s) ? s->S[k] : 0.0, F);
+  node_force_s(s, s->ncls > 1 ? s->ctot[k] : s->c[k], sugar_on(s) ? s->S[k] : 0.0, F);
 }
 
-/* Settling velocity at node k: Vs, or Vs (1 - kS S_k) with sugar. */
+/* Settling velocity at node k of the class being transported: Vs, or Vs (1 - kS S_k) with
+ * sugar. */
 static double settling_at(const orc_sim *s, size_t k) {
-  return sugar_on(s) ? s->p.settling_velocity * (1.0 - s->p.vs_sugar * s->S[k]) : s->p.settling_velocity;
+  return sugar_on(s) ? s->vs_cur * (1.0 - s->p.vs_sugar * s->S[k]) : s->vs_cur;
+}
+
+/* Class k's concentration array. */
+static double *class_c(const orc_sim *s, int k) { return k == 0 ? s->c : s->cls + (size_t)(k - 1) * s->nn; }
+
+/* phi_tot / phi0 = sum of the classes, serial in class order. */
+static void sum_classes(orc_sim *s) {
+  if (s->ncls < 2) return;
+  for (size_t j = 0; j < s->nn; ++j) {
+    double acc = 0.0;
+    for (int k = 0; k < s->ncls; ++k) acc += class_c(s, k)[j];
+    s->ctot[j] = acc;
+  }
 }
 
 /* ---- a1 + a2: moments and BGK-Guo collision at every node ---- */
@@ -427,9 +451,9 @@ static double floor_outflow(const orc_sim *s, const double *c) {
 
 /* ---- a8 + a9: SSP-RK3 (S21-S23) with dt = 1, velocity frozen, deposit by b-weights ---- */
 
-static void rk3_transport(orc_sim *s) {
+static double rk3_transport(orc_sim *s, double *c) {
   const size_t nn = s->nn;
-  double *c = s->c, *c1 = s->c1, *c2 = s->c2, *L = s->L;
+  double *c1 = s->c1, *c2 = s->c2, *L = s->L;
   transport_rate(s, c, L);
   for (size_t k = 0; k < nn; ++k) c1[k] = c[k] + L[k];
   transport_rate(s, c1, L);
@@ -439,12 +463,23 @@ static void rk3_transport(orc_sim *s) {
     if (sugar_on(s))
       dep = floor_outflow(s, c) / 6.0 + floor_outflow(s, c1) / 6.0 + 2.0 * floor_outflow(s, c2) / 3.0;
     else
-      dep = s->p.settling_velocity *
-            (floor_sum(s, c) / 6.0 + floor_sum(s, c1) / 6.0 + 2.0 * floor_sum(s, c2) / 3.0);
+      dep = s->vs_cur * (floor_sum(s, c) / 6.0 + floor_sum(s, c1) / 6.0 + 2.0 * floor_sum(s, c2) / 3.0);
   }
   transport_rate(s, c2, L);
   for (size_t k = 0; k < nn; ++k) c[k] = c[k] / 3.0 + 2.0 * c2[k] / 3.0 + 2.0 * L[k] / 3.0;
-  s->deposit += dep;
+  return dep;
+}
+
+/* a4-a9 for every particle class, each with its own settling velocity and deposit. */
+static void transport_classes(orc_sim *s) {
+  for (int k = 0; k < s->ncls; ++k) {
+    s->vs_cur = s->ncls > 1 ? s->p.class_vs[k] : s->p.settling_velocity;
+    const double dep = rk3_transport(s, class_c(s, k));
+    s->cls_dep[k] += dep;
+    s->deposit += dep;
+  }
+  s->vs_cur = s->ncls > 1 ? s->p.class_vs[0] : s->p.settling_velocity;
+  sum_classes(s);
 }
 
 /* ---- s3: sugar, first-order upwind (S5 for u > 0, S6 for u < 0) per axis, explicit, in
@@ -490,7 +525,8 @@ static void sugar_transport(orc_sim *s) {
 static void check_state(orc_sim *s) {
   const size_t nn = s->nn;
   for (size_t k = 0; k < nn; ++k) {
-    if (!isfinite(s->c[k])) s->status = ORC_EUNSTABLE;
+    for (int m = 0; m < s->ncls; ++m)
+      if (!isfinite(class_c(s, m)[k])) s->status = ORC_EUNSTABLE;
     for (int d = 0; d < s->p.dim; ++d) {
       double ud = s->u[(size_t)d * nn + k];
       if (!isfinite(ud) || fabs(ud) > s->p.u_cap) s->status = ORC_EUNSTABLE;
@@ -513,7 +549,15 @@ orc_sim *orc_create(const orc_params *p) {
   s->n[2] = s->p.nz;
   s->vaxis = s->p.dim - 1;
   s->nn = (size_t)s->n[0] * s->n[1] * s->n[2];
-  s->alpha = s->p.lf_alpha > 0.0 ? s->p.lf_alpha : s->p.settling_velocity + s->p.u_cap;
+  if (s->p.n_classes > 8) {
+    free(s);
+    return NULL;
+  }
+  s->ncls = s->p.n_classes >= 2 ? s->p.n_classes : 1;
+  s->vs_cur = s->ncls > 1 ? s->p.class_vs[0] : s->p.settling_velocity;
+  double vs_max = s->p.settling_velocity;
+  for (int k = 0; k < s->ncls && s->ncls > 1; ++k) vs_max = k == 0 || s->p.class_vs[k] > vs_max ? s->p.class_vs[k] : vs_max;
+  s->alpha = s->p.lf_alpha > 0.0 ? s->p.lf_alpha : vs_max + s->p.u_cap;
   s->eps = 1e-6 * s->alpha * s->alpha;
   if (s->p.dim == 2)
     set_d2q9(s);
@@ -532,10 +576,13 @@ orc_sim *orc_create(const orc_params *p) {
   s->u = (double *)calloc((size_t)s->p.dim * nn, sizeof(double));
   s->S = (double *)calloc(nn, sizeof(double));
   s->Snew = (double *)calloc(nn, sizeof(double));
+  s->cls = (double *)calloc((size_t)s->ncls * nn, sizeof(double)); /* classes 1.. (one spare) */
+  s->ctot = (double *)calloc(nn, sizeof(double));
   if (!s->f || !s->fpost || !s->c || !s->c1 || !s->c2 || !s->L || !s->flux || !s->rho || !s->u || !s->S ||
-      !s->Snew) {
+      !s->Snew || !s->cls || !s->ctot) {
     free(s->f); free(s->fpost); free(s->c); free(s->c1); free(s->c2);
-    free(s->L); free(s->flux); free(s->rho); free(s->u); free(s->S); free(s->Snew); free(s);
+    free(s->L); free(s->flux); free(s->rho); free(s->u); free(s->S); free(s->Snew);
+    free(s->cls); free(s->ctot); free(s);
     return NULL;
   }
   return s;
@@ -545,6 +592,7 @@ void orc_destroy(orc_sim *s) {
   if (!s) return;
   free(s->f); free(s->fpost); free(s->c); free(s->c1); free(s->c2);
   free(s->L); free(s->flux); free(s->rho); free(s->u); free(s->S); free(s->Snew);
+  free(s->cls); free(s->ctot);
   free(s);
 }
 
@@ -569,6 +617,9 @@ int orc_init(orc_sim *s, const double *c0, const double *u0) {
     s->rho[k] = 1.0;
   }
   memset(s->S, 0, nn * sizeof(double));
+  memset(s->cls, 0, (size_t)s->ncls * nn * sizeof(double));
+  memset(s->cls_dep, 0, sizeof(s->cls_dep));
+  sum_classes(s);
   s->deposit = 0.0;
   s->steps = 0;
   s->status = ORC_OK;
@@ -584,6 +635,23 @@ int orc_set_sugar(orc_sim *s, const double *S0) {
 
 void orc_sugar(const orc_sim *s, double *S) { memcpy(S, s->S, s->nn * sizeof(double)); }
 
+/* Particle class k (polydisperse): set after orc_init (which puts c0 in class 0 and zeros
+ * the others), read, and its deposit. */
+int orc_set_class(orc_sim *s, int k, const double *ck) {
+  if (!s || !ck || k < 0 || k >= s->ncls) return ORC_EINVAL;
+  memcpy(class_c(s, k), ck, s->nn * sizeof(double));
+  sum_classes(s);
+  return ORC_OK;
+}
+
+int orc_class(const orc_sim *s, int k, double *out) {
+  if (!s || !out || k < 0 || k >= s->ncls) return ORC_EINVAL;
+  memcpy(out, class_c(s, k), s->nn * sizeof(double));
+  return ORC_OK;
+}
+
+double orc_class_deposit(const orc_sim *s, int k) { return (k >= 0 && k < s->ncls) ? s->cls_dep[k] : 0.0; }
+
 /* One coupled step = a1..a3 on the populations (unless the velocity is frozen),
  * then a4..a9 on c with the velocity of a1 (O7: u at time n, frozen over the stages). */
 int orc_step(orc_sim *s, int64_t nsteps) {
@@ -593,7 +661,7 @@ int orc_step(orc_sim *s, int64_t nsteps) {
       collide_all(s);
       stream_all(s);
     }
-    rk3_transport(s);
+    transport_classes(s);
     if (sugar_on(s)) sugar_transport(s);
     check_state(s);
     s->steps++;
@@ -624,7 +692,7 @@ void orc_fields(const orc_sim *s, double *rho, double *u, double *c) {
       if (u)
         for (int d = 0; d < s->p.dim; ++d) u[(size_t)d * nn + k] = (mom[d] + 0.5 * F[d]) / r;
     }
-    if (c) c[k] = s->c[k];
+    if (c) c[k] = s->ncls > 1 ? s->ctot[k] : s->c[k];
   }
 }
 
@@ -647,7 +715,7 @@ double orc_alpha(const orc_sim *s) { return s->alpha; }
 /* Total c over the domain, serial and in index order. */
 double orc_total_mass(const orc_sim *s) {
   double acc = 0.0;
-  for (size_t k = 0; k < s->nn; ++k) acc += s->c[k];
+  for (size_t k = 0; k < s->nn; ++k) acc += s->ncls > 1 ? s->ctot[k] : s->c[k];
   return acc;
 }
 
@@ -887,6 +955,7 @@ int orc_deposit_gradient(const orc_params *p, const double *c0, int64_t nsteps, 
   if (!p || !c0 || !grad_c0 || !dJ_dVs || !J || nsteps < 1) return ORC_EINVAL;
   if (p->dim != 2 ||
       (p->flags & (ORC_PERIODIC_VERTICAL | ORC_FROZEN_VELOCITY | ORC_SUGAR | ORC_WENO3 | ORC_SIGN_SPLIT)) ||
+      p->n_classes >= 2 ||
       !(p->lf_alpha > 0.0))
     return ORC_EINVAL;
   orc_sim *s = orc_create(p);
