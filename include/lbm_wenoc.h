@@ -82,6 +82,12 @@ typedef struct {
   double sugar_diffusivity;  /* D_s >= 0 */
   double phi0;               /* particle volume fraction at c = 1, in the (1 - phi) factor of Eq. forceterm */
   double vs_sugar;           /* kS: settling velocity Vs (1 - kS S) (Eq. stokes_vel with rho(S)) */
+  /* polydisperse particles (Eqs. forceterm_poly, poly): n_classes >= 2 classes c_k, class k
+   * settling at class_vs[k] (settling_velocity unused), each with its own deposit; the force
+   * reads phi_tot = sum_k c_k.  0 or 1: one class.  At most 8; not with LW_FUSED_RK3,
+   * batches or the gradient.  The default lf_alpha takes the largest class velocity. */
+  int32_t n_classes;
+  double class_vs[8];
 } lbm_wenoc_params;
 
 /* Bytes of device workspace a handle with these parameters needs (populations,
@@ -211,6 +217,14 @@ int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int
  * Both synchronise. */
 int lbm_wenoc_set_sugar(lbm_wenoc* h, const void* S0);
 int lbm_wenoc_sugar(lbm_wenoc* h, void* S_out);
+
+/* Particle classes (n_classes >= 2): lbm_wenoc_init puts c0 in class 0 and zeroes the
+ * others; set class k (0 <= k < n_classes) after init, read it back, read its deposit.
+ * lbm_wenoc_fields and lbm_wenoc_total_mass report the sum of the classes and
+ * lbm_wenoc_deposited_mass the total deposit.  Host or device buffers; synchronise. */
+int lbm_wenoc_set_class(lbm_wenoc* h, int32_t k, const void* ck);
+int lbm_wenoc_class(lbm_wenoc* h, int32_t k, void* out);
+int lbm_wenoc_class_deposit(lbm_wenoc* h, int32_t k, double* out);
 
 /* Sum of a concentration field, FP64, for callers that cannot allocate device memory
  * (an application that owns a fixed device arena, a plugin inside another framework's

@@ -53,8 +53,14 @@ static_assert(lattice_ok<D3Q19>(), "D3Q19 table");
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t g, c, c1, c2, u, partials, scalars, status, sa, sb, total;
+  size_t g, c, c1, c2, u, partials, scalars, status, sa, sb, cls, ctot, total;
 };
+
+// scalars[0] deposit (one class), [1] reduction result, [4 + k] deposit of class k
+constexpr int kScalars = 16;
+constexpr int kClassDeposit = 4;
+
+int classes_of(const lbm_wenoc_params& p) { return p.n_classes >= 2 ? p.n_classes : 1; }
 
 Layout make_layout(const lbm_wenoc_params& p) {
   const size_t n = (size_t)p.nx * p.ny * (p.dim == 3 ? p.nz : 1);
@@ -73,11 +79,14 @@ Layout make_layout(const lbm_wenoc_params& p) {
   L.c2 = take(n * es);
   L.u = take((size_t)p.dim * n * es);
   L.partials = take(sizeof(double) * lw::kMaxReduceBlocks);
-  L.scalars = take(sizeof(double) * 4);
+  L.scalars = take(sizeof(double) * kScalars);
   L.status = take(sizeof(unsigned) * 4);
   const bool sugar = (p.flags & LW_SUGAR) != 0;
   L.sa = take(sugar ? n * es : 0);  // sugar of step n and n + 1 (ping-pong)
   L.sb = take(sugar ? n * es : 0);
+  const int ncls = classes_of(p);
+  L.cls = take(ncls > 1 ? (size_t)(ncls - 1) * align_up(n * es, 256) : 0);  // classes 1..ncls-1
+  L.ctot = take(ncls > 1 ? n * es : 0);                                   // their sum with class 0
   L.total = off;
   return L;
 }
@@ -93,6 +102,12 @@ int check_params(const lbm_wenoc_params* p) {
   if (!(p->settling_velocity >= 0.0) || !(p->diffusivity >= 0.0)) return LW_EINVAL;
   if (!(p->lf_alpha >= 0.0) || !(p->u_cap >= 0.0)) return LW_EINVAL;
   if ((p->flags & (LW_WENO3 | LW_SIGN_SPLIT)) && (p->flags & LW_FUSED_RK3)) return LW_EINVAL;
+  if (p->n_classes < 0 || p->n_classes > 8) return LW_EINVAL;
+  if (p->n_classes >= 2) {
+    if (p->flags & LW_FUSED_RK3) return LW_EINVAL;
+    for (int k = 0; k < p->n_classes; ++k)
+      if (!(p->class_vs[k] >= 0.0) || !std::isfinite(p->class_vs[k])) return LW_EINVAL;
+  }
   if ((p->flags & LW_SUGAR) && ((p->flags & LW_FUSED_RK3) || !(p->sugar_diffusivity >= 0.0) ||
                                 !std::isfinite(p->sugar_contrast) || !std::isfinite(p->phi0) ||
                                 !std::isfinite(p->vs_sugar)))
@@ -123,6 +138,7 @@ struct lbm_wenoc {
   int stage2d_rows = 0;
   bool initialised = false;
   bool sugar = false;  // LW_SUGAR: S in L.sa / L.sb, selected by cur (the generic transport path)
+  int ncls = 1;        // particle classes
   int64_t steps = 0;
   int64_t launches = 0;
   double alpha = 0.0;
@@ -255,34 +271,70 @@ void enqueue_sugar(lbm_wenoc* h, const Args<T>& a) {
   h->cur ^= 1;
 }
 
+// Particle class k's concentration buffer (class 0 is c).
+template <typename T>
+T* class_ptr(const lbm_wenoc* h, int k) {
+  if (k == 0) return reinterpret_cast<T*>(h->ws + h->L.c);
+  const size_t stride = align_up((size_t)h->n * sizeof(T), 256);
+  return reinterpret_cast<T*>(h->ws + h->L.cls + (size_t)(k - 1) * stride);
+}
+
+// phi_tot / phi0 = sum of the classes, into L.ctot (the force's concentration).
+template <typename T>
+void enqueue_class_sum(lbm_wenoc* h) {
+  lw::ClassPtrs<T> cp{};
+  cp.count = h->ncls;
+  for (int k = 0; k < h->ncls; ++k) cp.c[k] = class_ptr<T>(h, k);
+  const long long n = h->n;
+  T* out = reinterpret_cast<T*>(h->ws + h->L.ctot);
+  launch(h, K_OTHER, [&] {
+    lw::class_sum_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(cp, out, n);
+  });
+}
+
 template <class LAT, typename T>
 void enqueue_step(lbm_wenoc* h, int parity) {
   Args<T> a = make_args<T>(h);
   const dim3 blk(kLbmThreads);
   const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
   cudaStream_t s = h->stream;
+  Args<T> af = a;  // the fluid step's force reads phi_tot with several classes
+  if (h->ncls > 1) af.c = reinterpret_cast<T*>(h->ws + h->L.ctot);
   if (!h->frozen) {
     launch(h, K_LBM, [&] {
       if (LAT::DIM == 2) {
         if (h->sugar)
-          parity == 0 ? lw::lbm_d2q9_kernel<T, 0, true><<<grd, blk, 0, s>>>(a)
-                      : lw::lbm_d2q9_kernel<T, 1, true><<<grd, blk, 0, s>>>(a);
+          parity == 0 ? lw::lbm_d2q9_kernel<T, 0, true><<<grd, blk, 0, s>>>(af)
+                      : lw::lbm_d2q9_kernel<T, 1, true><<<grd, blk, 0, s>>>(af);
         else if (parity == 0)
-          lw::lbm_d2q9_kernel<T, 0><<<grd, blk, 0, s>>>(a);
+          lw::lbm_d2q9_kernel<T, 0><<<grd, blk, 0, s>>>(af);
         else
-          lw::lbm_d2q9_kernel<T, 1><<<grd, blk, 0, s>>>(a);
+          lw::lbm_d2q9_kernel<T, 1><<<grd, blk, 0, s>>>(af);
       } else {
         if (h->sugar)
-          parity == 0 ? lw::lbm_d3q19_kernel<T, 0, true><<<grd, blk, 0, s>>>(a)
-                      : lw::lbm_d3q19_kernel<T, 1, true><<<grd, blk, 0, s>>>(a);
+          parity == 0 ? lw::lbm_d3q19_kernel<T, 0, true><<<grd, blk, 0, s>>>(af)
+                      : lw::lbm_d3q19_kernel<T, 1, true><<<grd, blk, 0, s>>>(af);
         else if (parity == 0)
-          lw::lbm_d3q19_kernel<T, 0><<<grd, blk, 0, s>>>(a);
+          lw::lbm_d3q19_kernel<T, 0><<<grd, blk, 0, s>>>(af);
         else
-          lw::lbm_d3q19_kernel<T, 1><<<grd, blk, 0, s>>>(a);
+          lw::lbm_d3q19_kernel<T, 1><<<grd, blk, 0, s>>>(af);
       }
     });
   }
-  enqueue_transport<LAT, T>(h, a);
+  if (h->ncls == 1) {
+    enqueue_transport<LAT, T>(h, a);
+  } else {
+    // each class with its own settling velocity and deposit slot
+    for (int k = 0; k < h->ncls; ++k) {
+      Args<T> ak = a;
+      ak.c = class_ptr<T>(h, k);
+      ak.vs = T(h->p.class_vs[k]);
+      ak.scalars = a.scalars + kClassDeposit + k;
+      enqueue_transport<LAT, T>(h, ak);
+    }
+    enqueue_class_sum<T>(h);
+  }
+  enqueue_sugar<LAT, T>(h, a);
 }
 
 // The three RK stages (and the deposit) of one step on the fields a points at.
@@ -306,7 +358,6 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
     launch(h, K_STAGE1, [&] { lw::launch_stage2d<1>(af, af.c, af.c1, H, s); });
     launch(h, K_STAGE2, [&] { lw::launch_stage2d<2>(af, af.c1, af.c2, H, s); });
     launch(h, K_STAGE3, [&] { lw::launch_stage2d<3>(af, af.c2, af.c, H, s); });  // + deposit
-    enqueue_sugar<LAT, T>(h, a);
     return;
   }
   if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d) {
@@ -327,7 +378,6 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
       lw::deposit_kernel<T><<<dep_blocks, lw::kReduceThreads, 0, s>>>(a, nfloor);
     });
   launch(h, K_STAGE3, [&] { lw::rk_stage_kernel<T, LAT::DIM, 3><<<grd, blk, 0, s>>>(a); });
-  enqueue_sugar<LAT, T>(h, a);
 }
 
 void enqueue_one(lbm_wenoc* h, int parity) {
@@ -377,8 +427,9 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
 
 int launches_per_step(const lbm_wenoc* h) {
   if (h->sweep) return h->frozen ? 1 : 2;
-  if (h->stage2d) return (h->frozen ? 0 : 1) + 3 + (h->sugar ? 1 : 0);
-  return (h->frozen ? 0 : 1) + 3 + (h->walls ? 1 : 0) + (h->sugar ? 1 : 0);
+  const int classes = h->ncls > 1 ? h->ncls : 1, sum = h->ncls > 1 ? 1 : 0;
+  const int per_class = (h->stage2d || h->sweep3d) ? (h->sweep3d ? 4 : 3) : 3 + (h->walls ? 1 : 0);
+  return (h->frozen ? 0 : 1) + classes * per_class + sum + (h->sugar ? 1 : 0);
 }
 
 int sync_and_status(lbm_wenoc* h) {
@@ -402,6 +453,7 @@ bool is_device_pointer(const void* p) {
 template <class LAT, typename T>
 void launch_fields(lbm_wenoc* h, T* rho, T* u) {
   Args<T> a = make_args<T>(h);
+  if (h->ncls > 1) a.c = reinterpret_cast<T*>(h->ws + h->L.ctot);  // the force reads phi_tot
   const dim3 blk(kLbmThreads);
   const dim3 grd((a.nx + kLbmThreads - 1) / kLbmThreads, a.ny, a.nz);
   if (h->parity == 0)
@@ -460,7 +512,13 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   const bool variant = (p->flags & (LW_WENO3 | LW_SIGN_SPLIT)) != 0;  // generic stage kernels
   h->use_graphs = (p->flags & LW_NO_GRAPH) == 0;
   h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
-  h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : p->settling_velocity + h->p.u_cap;
+  h->ncls = classes_of(*p);
+  double vs_max = p->settling_velocity;
+  if (h->ncls > 1) {
+    vs_max = p->class_vs[0];
+    for (int k = 1; k < h->ncls; ++k) vs_max = std::max(vs_max, p->class_vs[k]);
+  }
+  h->alpha = p->lf_alpha > 0.0 ? p->lf_alpha : vs_max + h->p.u_cap;
   cudaGetDevice(&h->device);
   h->sweep = !h->fp64 && !variant && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
@@ -514,9 +572,16 @@ int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
     if (cudaMemcpyAsync(h->ws + h->L.u, u0, ubytes, ku, h->stream) != cudaSuccess) return LW_ECUDA;
     u0dev = h->ws + h->L.u;
   }
-  if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * kScalars, h->stream) != cudaSuccess)
+    return LW_ECUDA;
   if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
   if (h->sugar && cudaMemsetAsync(h->ws + h->L.sa, 0, cbytes, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (h->ncls > 1) {  // c0 is class 0; the others start empty, so phi_tot = c0
+    if (cudaMemsetAsync(h->ws + h->L.cls, 0, h->L.ctot - h->L.cls, h->stream) != cudaSuccess) return LW_ECUDA;
+    if (cudaMemcpyAsync(h->ws + h->L.ctot, h->ws + h->L.c, cbytes, cudaMemcpyDeviceToDevice, h->stream) !=
+        cudaSuccess)
+      return LW_ECUDA;
+  }
   if (h->p.dim == 2) {
     if (h->fp64)
       launch_init<D2Q9, double>(h, static_cast<const double*>(u0dev));
@@ -584,6 +649,14 @@ int lbm_wenoc_deposited_mass(lbm_wenoc* h, double* out) {
   if (!h->initialised) return LW_ESTATE;
   int rc = sync_and_status(h);
   if (rc == LW_ECUDA) return rc;
+  if (h->ncls > 1) {
+    double dep[kScalars];
+    if (cudaMemcpy(dep, h->ws + h->L.scalars, sizeof(dep), cudaMemcpyDeviceToHost) != cudaSuccess) return LW_ECUDA;
+    double tot = 0.0;
+    for (int k = 0; k < h->ncls; ++k) tot += dep[kClassDeposit + k];
+    *out = tot;
+    return rc;
+  }
   if (cudaMemcpy(out, h->ws + h->L.scalars, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LW_ECUDA;
   return rc;
@@ -593,12 +666,15 @@ int lbm_wenoc_total_mass(lbm_wenoc* h, double* out) {
   if (!h || !out) return LW_EINVAL;
   if (!h->initialised) return LW_ESTATE;
   const int blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (h->n + 8191) / 8192);
+  const bool classes = h->ncls > 1;  // the sum of the classes
   if (h->fp64) {
     Args<double> a = make_args<double>(h);
-    lw::sum_kernel<double><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, a.c, h->n);
+    const double* src = classes ? reinterpret_cast<const double*>(h->ws + h->L.ctot) : a.c;
+    lw::sum_kernel<double><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, src, h->n);
   } else {
     Args<float> a = make_args<float>(h);
-    lw::sum_kernel<float><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, a.c, h->n);
+    const float* src = classes ? reinterpret_cast<const float*>(h->ws + h->L.ctot) : a.c;
+    lw::sum_kernel<float><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, src, h->n);
   }
   if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
@@ -646,7 +722,8 @@ int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
   };
   if (rho && !copy_out(rho, rho_dev, cbytes)) return LW_ECUDA;
   if (u && !copy_out(u, u_dev, cbytes * h->p.dim)) return LW_ECUDA;
-  if (c && !copy_out(c, h->ws + (h->sweep && h->cur ? h->L.c1 : h->L.c), cbytes)) return LW_ECUDA;
+  const size_t c_off = h->ncls > 1 ? h->L.ctot : (h->sweep && h->cur ? h->L.c1 : h->L.c);
+  if (c && !copy_out(c, h->ws + c_off, cbytes)) return LW_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
   return LW_OK;
 }
@@ -668,6 +745,41 @@ int lbm_wenoc_set_sugar(lbm_wenoc* h, const void* S0) {
   if (cudaMemcpyAsync(h->ws + (h->cur ? h->L.sb : h->L.sa), S0, bytes, k, h->stream) != cudaSuccess)
     return LW_ECUDA;
   return cudaStreamSynchronize(h->stream) == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+int lbm_wenoc_set_class(lbm_wenoc* h, int32_t k, const void* ck) {
+  if (!h || !ck || h->ncls < 2 || k < 0 || k >= h->ncls) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const size_t bytes = (size_t)h->n * (h->fp64 ? 8 : 4);
+  void* dst = h->fp64 ? (void*)class_ptr<double>(h, k) : (void*)class_ptr<float>(h, k);
+  cudaMemcpyKind kind = is_device_pointer(ck) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(dst, ck, bytes, kind, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (h->fp64)
+    enqueue_class_sum<double>(h);
+  else
+    enqueue_class_sum<float>(h);
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+int lbm_wenoc_class(lbm_wenoc* h, int32_t k, void* out) {
+  if (!h || !out || h->ncls < 2 || k < 0 || k >= h->ncls) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const size_t bytes = (size_t)h->n * (h->fp64 ? 8 : 4);
+  const void* src = h->fp64 ? (const void*)class_ptr<double>(h, k) : (const void*)class_ptr<float>(h, k);
+  cudaMemcpyKind kind = is_device_pointer(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (cudaMemcpyAsync(out, src, bytes, kind, h->stream) != cudaSuccess) return LW_ECUDA;
+  return sync_and_status(h);
+}
+
+int lbm_wenoc_class_deposit(lbm_wenoc* h, int32_t k, double* out) {
+  if (!h || !out || h->ncls < 2 || k < 0 || k >= h->ncls) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  int rc = sync_and_status(h);
+  if (rc == LW_ECUDA) return rc;
+  if (cudaMemcpy(out, h->ws + h->L.scalars + sizeof(double) * (kClassDeposit + k), sizeof(double),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LW_ECUDA;
+  return rc;
 }
 
 int lbm_wenoc_sugar(lbm_wenoc* h, void* S_out) {
@@ -765,7 +877,7 @@ namespace {
 
 bool batch_params_ok(const lbm_wenoc_params& p) {
   return check_params(&p) == LW_OK && p.dim == 2 && !(p.flags & LW_FP64) && !(p.flags & LW_PERIODIC_VERTICAL) &&
-         !(p.flags & (LW_FROZEN_VELOCITY | LW_FUSED_RK3 | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT)) &&
+         !(p.flags & (LW_FROZEN_VELOCITY | LW_FUSED_RK3 | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT)) && p.n_classes < 2 &&
          (p.nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
 }
 
@@ -952,7 +1064,8 @@ int lbm_wenoc_batch_autotune(lbm_wenoc_batch* b, int32_t steps_per_trial, int32_
   // trial state: c = 0 and the fluid at rest in every instance (the caller inits afterwards)
   for (lbm_wenoc* h : b->inst) {
     if (cudaMemsetAsync(h->ws + h->L.c, 0, (size_t)h->n * sizeof(float), b->stream) != cudaSuccess) return LW_ECUDA;
-    if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * 4, b->stream) != cudaSuccess) return LW_ECUDA;
+    if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * kScalars, b->stream) != cudaSuccess)
+      return LW_ECUDA;
     if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, b->stream) != cudaSuccess) return LW_ECUDA;
     h->cur = 0;
     launch_init<D2Q9, float>(h, nullptr);
@@ -1018,7 +1131,7 @@ namespace {
 
 bool gradient_params_ok(const lbm_wenoc* h) {
   return h && h->p.dim == 2 && h->walls && !h->frozen && !h->sweep && !h->sugar &&
-         !(h->p.flags & (LW_WENO3 | LW_SIGN_SPLIT)) && h->p.lf_alpha > 0.0;
+         !(h->p.flags & (LW_WENO3 | LW_SIGN_SPLIT)) && h->ncls == 1 && h->p.lf_alpha > 0.0;
 }
 
 struct GradLayout {

@@ -72,4 +72,21 @@ __global__ void __launch_bounds__(kReduceThreads) sum_kernel(Args<T> a, const T*
   finish_reduction(s, a.partials, a.ticket, &a.scalars[1], 0);
 }
 
+// Polydisperse particles: phi_tot / phi0 = sum of the classes (in class order), the
+// concentration the force reads (Eqs. forceterm_poly, poly).
+template <typename T>
+struct ClassPtrs {
+  const T* c[8];
+  int count;
+};
+
+template <typename T>
+__global__ void class_sum_kernel(ClassPtrs<T> cp, T* out, long long n) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  T acc = cp.c[0][k];
+  for (int m = 1; m < cp.count; ++m) acc += cp.c[m][k];
+  out[k] = acc;
+}
+
 }  // namespace lw

@@ -42,7 +42,7 @@ EXPORTED = [
     "lbm_wenoc_batch_instance", "lbm_wenoc_batch_step", "lbm_wenoc_batch_autotune",
     "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy",
     "lbm_wenoc_gradient_workspace_bytes", "lbm_wenoc_deposit_gradient", "lbm_wenoc_set_sugar",
-    "lbm_wenoc_sugar",
+    "lbm_wenoc_sugar", "lbm_wenoc_set_class", "lbm_wenoc_class", "lbm_wenoc_class_deposit",
 ]
 
 
@@ -71,6 +71,8 @@ class lbm_wenoc_params(ctypes.Structure):
         ("sugar_diffusivity", ctypes.c_double),
         ("phi0", ctypes.c_double),
         ("vs_sugar", ctypes.c_double),
+        ("n_classes", ctypes.c_int32),
+        ("class_vs", ctypes.c_double * 8),
     ]
 
 
@@ -130,6 +132,9 @@ def load():
     L.lbm_wenoc_deposit_gradient.argtypes = [vp, vp, i64, ctypes.c_int32, vp, ctypes.c_size_t, vp, dp, dp]
     L.lbm_wenoc_set_sugar.argtypes = [vp, vp]
     L.lbm_wenoc_sugar.argtypes = [vp, vp]
+    L.lbm_wenoc_set_class.argtypes = [vp, ctypes.c_int32, vp]
+    L.lbm_wenoc_class.argtypes = [vp, ctypes.c_int32, vp]
+    L.lbm_wenoc_class_deposit.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTED:
         if name not in ("lbm_wenoc_steps", "lbm_wenoc_launch_count", "lbm_wenoc_destroy",
                         "lbm_wenoc_batch_instance", "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy"):
@@ -256,6 +261,20 @@ def lbm_wenoc_sugar(h, S_out):
     return _check("lbm_wenoc_sugar", load().lbm_wenoc_sugar(h, _ptr(S_out)))
 
 
+def lbm_wenoc_set_class(h, k, ck):
+    return _check("lbm_wenoc_set_class", load().lbm_wenoc_set_class(h, int(k), _ptr(ck)))
+
+
+def lbm_wenoc_class(h, k, out):
+    return _check("lbm_wenoc_class", load().lbm_wenoc_class(h, int(k), _ptr(out)))
+
+
+def lbm_wenoc_class_deposit(h, k):
+    out = ctypes.c_double()
+    _check("lbm_wenoc_class_deposit", load().lbm_wenoc_class_deposit(h, int(k), ctypes.byref(out)))
+    return out.value
+
+
 def default_segment(nsteps):
     """Checkpoint spacing that minimises the stored states (checkpoints + one segment)."""
     return max(1, int(round(float(nsteps) ** 0.5)))
@@ -272,7 +291,7 @@ def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velo
                 diffusivity=0.0, lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), fp64=False,
                 periodic_vertical=False, frozen_velocity=False, graphs=True, fused_rk3=False,
                 sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0,
-                weno3=False, sign_split=False):
+                weno3=False, sign_split=False, class_vs=()):
     p = lbm_wenoc_params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -286,6 +305,9 @@ def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velo
                (LW_FUSED_RK3 if fused_rk3 else 0) | (LW_SUGAR if sugar else 0) | (LW_WENO3 if weno3 else 0) |
                (LW_SIGN_SPLIT if sign_split else 0))
     p.sugar_contrast, p.sugar_diffusivity, p.phi0, p.vs_sugar = sugar_contrast, sugar_diffusivity, phi0, vs_sugar
+    p.n_classes = len(class_vs)
+    for k, v in enumerate(class_vs):
+        p.class_vs[k] = float(v)
     return p
 
 
@@ -372,6 +394,19 @@ class Simulation:
         S = torch.empty(self.grid, dtype=self.dtype, device=device)
         lbm_wenoc_sugar(self.handle, S)
         return S
+
+    def set_class(self, k, ck):
+        """Particle class k of a polydisperse handle (after init)."""
+        lbm_wenoc_set_class(self.handle, k, self._as_input(ck, self.grid))
+
+    def class_field(self, k, device="cpu"):
+        import torch
+        out = torch.empty(self.grid, dtype=self.dtype, device=device)
+        lbm_wenoc_class(self.handle, k, out)
+        return out
+
+    def class_deposit(self, k):
+        return lbm_wenoc_class_deposit(self.handle, k)
 
     def deposit_gradient(self, c0, nsteps, segment=None):
         """Run nsteps from c0 (fluid at rest) and return (J, dJ/dc0, dJ/dVs): J the
