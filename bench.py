@@ -124,10 +124,10 @@ class ClockSampler:
 # taken on; a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
     "rk3_sweep2d": (127.72e6, "paper_2106_07694_gb300/csrc/transport_sweep2d.cuh", "83e0464e30c5"),
-    "lbm_collide_stream": (644.06e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "fa3b480929ff"),
-    "rk_stage1": (112.81e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "61f5d8230dc8"),
-    "rk_stage2": (151.05e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "61f5d8230dc8"),
-    "rk_stage3": (146.58e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "61f5d8230dc8"),
+    "lbm_collide_stream": (643.99e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "3d0cf7d72c36"),
+    "rk_stage1": (112.73e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
+    "rk_stage2": (150.98e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
+    "rk_stage3": (146.65e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
     # 512 x 1024 adjoint workload (the face records stay in L2)
     "adj_faces": (9.12e6, "paper_2106_07694_gb300/csrc/adjoint.cuh", "bb59bd120597"),
 }
