@@ -1122,7 +1122,7 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b) {
 // Gradient of the deposited mass by checkpoint-and-recompute and the adjoint kernels.
 //
 // Adjoint workspace: a checkpoint (populations + c, the handle's layout from g to c) at the
-// start of every segment but the last; one segment of step records (c before the step,
+// start of every segment but the last; two segments of step records (c before the step,
 // then the step's c1, c2, u and rho, which the recording steps write there directly);
 // lambda of the populations (two buffers, natural layout); mu, lc2, lc1, lc, lambda(u);
 // lambda(Vs) and its per-CTA partials; the face derivative records of one stage.
@@ -1137,6 +1137,8 @@ bool gradient_params_ok(const lbm_wenoc* h) {
 struct GradLayout {
   size_t ckpt, rec, lg0, lg1, mu, lc2, lc1, lc, lu, vs, vs_part, faces, total;
   size_t ckpt_bytes, field_bytes, rec_bytes;  // one checkpoint, one field, one step record
+  int rec_sets;                               // record sets (segments in flight)
+  int32_t segment;
   int nparts;                                 // per-CTA dJ/dVs partials of the face kernel
   int64_t nseg;
 };
@@ -1147,6 +1149,7 @@ GradLayout grad_layout(const lbm_wenoc_params& p, int64_t nsteps, int32_t segmen
   const size_t es = (p.flags & LW_FP64) ? 8 : 4;
   GradLayout G{};
   G.nseg = (nsteps + segment - 1) / segment;
+  G.segment = segment;
   G.ckpt_bytes = align_up(L.c + n * es - L.g, 256);
   G.field_bytes = align_up(n * es, 256);
   G.rec_bytes = 6 * G.field_bytes;  // c, c1, c2, u (2), rho
@@ -1157,7 +1160,8 @@ GradLayout grad_layout(const lbm_wenoc_params& p, int64_t nsteps, int32_t segmen
     return o;
   };
   G.ckpt = take(G.ckpt_bytes * (size_t)(G.nseg - 1));  // the last segment is recorded directly
-  G.rec = take(G.rec_bytes * (size_t)segment);
+  G.rec_sets = G.nseg > 1 ? 2 : 1;  // the recompute of a segment overlaps the reverse of the next
+  G.rec = take(G.rec_bytes * (size_t)segment * G.rec_sets);
   G.lg0 = take(9 * n * es);
   G.lg1 = take(9 * n * es);
   G.mu = take(n * es);
@@ -1182,9 +1186,10 @@ struct StepRecord {
   T *c, *c1, *c2, *u, *rho;
 };
 
+// Record of step k of a segment whose records live in set `set`.
 template <typename T>
-StepRecord<T> step_record(unsigned char* aw, const GradLayout& G, int64_t k) {
-  unsigned char* r = aw + G.rec + (size_t)k * G.rec_bytes;
+StepRecord<T> step_record(unsigned char* aw, const GradLayout& G, int set, int64_t k) {
+  unsigned char* r = aw + G.rec + ((size_t)set * (size_t)G.segment + (size_t)k) * G.rec_bytes;
   StepRecord<T> R;
   R.c = reinterpret_cast<T*>(r);
   R.c1 = reinterpret_cast<T*>(r + G.field_bytes);
@@ -1240,6 +1245,28 @@ int adjoint_step(lbm_wenoc* h, const StepRecord<T>& R, const lw::AdjFields<T>& f
   return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
+// A second stream and its events for the recompute that overlaps the reverse sweep.
+struct RecomputeStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t rec_done[2] = {nullptr, nullptr};  // records of set i written
+  cudaEvent_t rev_done[2] = {nullptr, nullptr};  // records of set i no longer read
+  bool ok = false;
+  RecomputeStream() {
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+      ok = cudaEventCreateWithFlags(&rec_done[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&rev_done[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  ~RecomputeStream() {
+    if (s) cudaStreamSynchronize(s);
+    for (int i = 0; i < 2; ++i) {
+      if (rec_done[i]) cudaEventDestroy(rec_done[i]);
+      if (rev_done[i]) cudaEventDestroy(rev_done[i]);
+    }
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 template <typename T>
 int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t segment, unsigned char* aw,
                           const GradLayout& G, void* grad_c0, double* dJ_dVs, double* J) {
@@ -1249,9 +1276,11 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   const Layout& L = h->L;
   unsigned char* state = h->ws + L.g;
   const size_t n = (size_t)h->n;
-  auto record_segment = [&](int64_t len) -> int {
-    for (int64_t k = 0; k < len; ++k) {
-      const int r = record_step<T>(h, step_record<T>(aw, G, k));
+  auto seg_len = [&](int64_t sg) { return std::min<int64_t>(segment, nsteps - sg * segment); };
+  auto set_of = [&](int64_t sg) { return G.rec_sets > 1 ? (int)(sg & 1) : 0; };
+  auto record_segment = [&](int64_t sg) -> int {
+    for (int64_t k = 0; k < seg_len(sg); ++k) {
+      const int r = record_step<T>(h, step_record<T>(aw, G, set_of(sg), k));
       if (r != LW_OK) return r;
     }
     return LW_OK;
@@ -1260,17 +1289,16 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   // recorded on the way (it is the first one the reverse sweep needs)
   std::vector<int> ck_parity((size_t)G.nseg);
   for (int64_t sg = 0; sg < G.nseg; ++sg) {
-    const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
     ck_parity[(size_t)sg] = h->parity;
     if (sg == G.nseg - 1) {
-      rc = record_segment(len);
+      rc = record_segment(sg);
     } else {
       rc = copy_d2d(aw + G.ckpt + (size_t)sg * G.ckpt_bytes, state, G.ckpt_bytes, s);
-      if (rc == LW_OK) rc = lbm_wenoc_step(h, len);
+      if (rc == LW_OK) rc = lbm_wenoc_step(h, seg_len(sg));
     }
     if (rc != LW_OK) return rc;
   }
-  if ((rc = lbm_wenoc_deposited_mass(h, J)) != LW_OK) return rc;
+  if ((rc = lbm_wenoc_deposited_mass(h, J)) != LW_OK) return rc;  // synchronises
   lw::AdjFields<T> f;
   f.mu = reinterpret_cast<T*>(aw + G.mu);
   f.lc2 = reinterpret_cast<T*>(aw + G.lc2);
@@ -1291,19 +1319,36 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
     lw::adj_init_kernel<T><<<(unsigned)((std::max<size_t>(n, (size_t)nparts) + 255) / 256), 256, 0, s>>>(
         f, (long long)n, nparts);
   });
-  int cur = 0;
-  for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
-    const int64_t len = std::min<int64_t>(segment, nsteps - sg * segment);
-    if (sg != G.nseg - 1) {  // recompute the segment from its checkpoint, recording it
-      if ((rc = copy_d2d(state, aw + G.ckpt + (size_t)sg * G.ckpt_bytes, G.ckpt_bytes, s)) != LW_OK) return rc;
+  // Reverse sweep over the segments, last first.  Segment sg's records sit in set sg & 1;
+  // while the reverse of sg runs on the handle's stream, the recompute of sg - 1 runs on a
+  // second stream into the other set, after the reverse of sg + 1 has released it.
+  RecomputeStream rs;
+  if (G.nseg > 1 && !rs.ok) return LW_ECUDA;
+  auto recompute = [&](int64_t sg) -> int {
+    h->stream = rs.s;
+    int r = LW_OK;
+    // set sg & 1 was last read by the reverse of segment sg + 2
+    if (sg + 2 <= G.nseg - 1 && cudaStreamWaitEvent(rs.s, rs.rev_done[set_of(sg)], 0) != cudaSuccess) r = LW_ECUDA;
+    if (r == LW_OK) r = copy_d2d(state, aw + G.ckpt + (size_t)sg * G.ckpt_bytes, G.ckpt_bytes, rs.s);
+    if (r == LW_OK) {
       h->parity = ck_parity[(size_t)sg];
       h->cur = 0;
-      if ((rc = record_segment(len)) != LW_OK) return rc;
+      r = record_segment(sg);
     }
-    for (int64_t k = len - 1; k >= 0; --k) {
-      if ((rc = adjoint_step<T>(h, step_record<T>(aw, G, k), f, fr, lg[cur], lg[cur ^ 1])) != LW_OK) return rc;
+    if (r == LW_OK && cudaEventRecord(rs.rec_done[set_of(sg)], rs.s) != cudaSuccess) r = LW_ECUDA;
+    h->stream = s;
+    return r;
+  };
+  int cur = 0;
+  for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
+    if (sg >= 1 && (rc = recompute(sg - 1)) != LW_OK) return rc;
+    if (sg != G.nseg - 1 && cudaStreamWaitEvent(s, rs.rec_done[set_of(sg)], 0) != cudaSuccess) return LW_ECUDA;
+    for (int64_t k = seg_len(sg) - 1; k >= 0; --k) {
+      if ((rc = adjoint_step<T>(h, step_record<T>(aw, G, set_of(sg), k), f, fr, lg[cur], lg[cur ^ 1])) != LW_OK)
+        return rc;
       cur ^= 1;
     }
+    if (G.nseg > 1 && cudaEventRecord(rs.rev_done[set_of(sg)], s) != cudaSuccess) return LW_ECUDA;
   }
   // mu now holds lambda(c^0)
   launch(h, K_OTHER, [&] { lw::adj_vs_finish_kernel<<<1, 256, 0, s>>>(f.vs_part, nparts, f.lam_vs); });
