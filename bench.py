@@ -31,6 +31,8 @@ WORKLOADS = {
     "3d": (workloads.MAIN_3D, "coupled LBM+WENO5 GLUPS (3D D3Q19 256x256x512 FP32)", "D3Q19"),
     "sugar": (workloads.SUGAR_2D, "coupled LBM+WENO5+sugar GLUPS (2D D2Q9 2048x4096 FP32, two-layer state)",
               "D2Q9"),
+    "small": (workloads.SMALL_2D, "coupled LBM+WENO5 GLUPS (2D D2Q9 128x256 FP64, L2-resident parity case)",
+              "D2Q9"),
 }
 WL, METRIC, LATTICE = WORKLOADS["2d"]
 ADJOINT_METRIC = ("gradient of the deposited mass wrt c0 and Vs, GLUPS of the reverse-mode pass "
@@ -222,9 +224,11 @@ def bench_ours(args):
     wl = WL
     kw = phys_kwargs(wl)
     stream = torch.cuda.current_stream()
-    sim = lw.Simulation(wl.shape, fp64=False, stream=stream, **kw)
-    c0 = wl.initial_c().astype(np.float32)
-    S0 = wl.initial_S().astype(np.float32) if wl.sugar else None
+    fp64 = wl.dtype == "f64"
+    np_dt = np.float64 if fp64 else np.float32
+    sim = lw.Simulation(wl.shape, fp64=fp64, stream=stream, **kw)
+    c0 = wl.initial_c().astype(np_dt)
+    S0 = wl.initial_S().astype(np_dt) if wl.sugar else None
     sim.init(torch.from_numpy(c0).to(dev))
     if S0 is not None:
         sim.set_sugar(torch.from_numpy(S0).to(dev))
@@ -273,8 +277,9 @@ def bench_ours(args):
     #   whole step     populations in and out + c in and out: 80 B (2D), 160 B (3D)
     # FP32 peak: 152 SMs x 128 lanes x 2 flop (FMA) x the sampled SM clock.
     dim = len(wl.shape)
-    lbm_B = 2 * (9 if dim == 2 else 19) * 4 + 4 + (4 if wl.sugar else 0)  # + S in (sugar force)
-    step_B = lbm_B + 4 + (4 if wl.sugar else 0)                               # + c out (+ S out)
+    es = 8 if fp64 else 4
+    lbm_B = 2 * (9 if dim == 2 else 19) * es + es + (es if wl.sugar else 0)  # + S in (sugar force)
+    step_B = lbm_B + es + (es if wl.sugar else 0)                               # + c out (+ S out)
     tr_flop = 915.0 if dim == 2 else 1371.0
     flop_of = {"rk3_sweep2d": tr_flop, "rk3_sweep3d": tr_flop, "rk_stage1": tr_flop / 3,
                "rk_stage2": tr_flop / 3, "rk_stage3": tr_flop / 3}
@@ -298,12 +303,18 @@ def bench_ours(args):
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                     "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": ncu_traffic.get(dominant), "alg_bytes_per_node": lbm_B}
+    if roofline and roofline.get("traffic"):  # ncu DRAM bytes per launch over the live duration
+        roofline["dram_gbs"] = roofline["traffic"] / avg_s(roofline["kernel"]) / 1e9
     lbm_roofline = None
     if "lbm_collide_stream" in stats:
         a_ = lbm_B * wl.nodes / avg_s("lbm_collide_stream") / 1e9
+        tr_ = ncu_traffic.get("lbm_collide_stream")
         lbm_roofline = {"bound": "hbm", "kernel": "lbm_collide_stream", "achieved": a_, "peak": peak,
-                        "unit": "GB/s", "frac": a_ / peak, "traffic": ncu_traffic.get("lbm_collide_stream"),
+                        "unit": "GB/s", "frac": a_ / peak, "traffic": tr_,
+                        "dram_gbs": tr_ / avg_s("lbm_collide_stream") / 1e9 if tr_ else None,
                         "alg_bytes_per_node": lbm_B}
+    if fp64:  # the L2-resident FP64 parity case: launch-bound, no roofline claim
+        roofline = {"bound": None, "note": "2.4 MB working set in L2: launch-bound parity case, no roofline claim"}
     # the transport as a whole (one fused kernel or three stage kernels) against the FP32 peak
     tr_kernels = [k for k in ("rk3_sweep2d", "rk_stage1", "rk_stage2", "rk_stage3") if k in stats]
     transport_roofline = None
@@ -322,7 +333,7 @@ def bench_ours(args):
     c_host = torch.from_numpy(c0).pin_memory()
     c_out = torch.empty_like(c_host).pin_memory()
     S_host = torch.from_numpy(S0).pin_memory() if S0 is not None else None
-    sim2 = lw.Simulation(wl.shape, fp64=False, stream=stream, **kw)
+    sim2 = lw.Simulation(wl.shape, fp64=fp64, stream=stream, **kw)
     sim2.init(c_host)
     if S_host is not None:
         sim2.set_sugar(S_host)
@@ -340,8 +351,9 @@ def bench_ours(args):
     barrier()
     e2e_s = job_time_ms(e2e_s * 1e3, device=dev) * 1e-3
     e2e = {"value": world * wl.nodes * args.steps / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": (c_host.numel() * 4 * (2 if S_host is not None else 1)) / args.steps,
-           "d2h_bytes_per_step": (c_out.numel() * 4 + 8) / args.steps,
+           "h2d_bytes_per_step": (c_host.numel() * c_host.element_size() * (2 if S_host is not None else 1))
+           / args.steps,
+           "d2h_bytes_per_step": (c_out.numel() * c_out.element_size() + 8) / args.steps,
            "note": "per job: H2D c0 (+ S0) + init + K steps + deposit (8 B) + D2H c, host wall clock"}
     assert np.isfinite(dep)
     sim2.close()
@@ -359,11 +371,13 @@ def bench_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
             "config": {"workload": wl.name, "shape": list(wl.shape), "lattice": LATTICE,
                        "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
                        "kappa": wl.diffusivity, "parallelism": f"replicas{world}", **({"sugar": wl.sugar} if wl.sugar else {}),
-                       "l2": f"inputs larger than L2 (populations {wl.nodes * (9 if len(wl.shape) == 2 else 19) * 4 / 1e6:.0f} MB)"},
+                       "l2": (lambda mb: f"inputs larger than L2 (populations {mb:.0f} MB)" if mb > 129
+                              else f"inputs fit in L2 (populations {mb:.1f} MB): no L2 flush claim")(
+                           wl.nodes * (9 if len(wl.shape) == 2 else 19) * (8 if fp64 else 4) / 1e6)},
             "roofline": roofline, "lbm_roofline": lbm_roofline, "transport_roofline": transport_roofline,
             "step_roofline": step_roofline,
             "kernels": kernels,

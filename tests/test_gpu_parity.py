@@ -137,6 +137,19 @@ def test_fp32_small_workload_before_saturation(fused):
     assert abs(g.deposit - o.deposit) <= 1e-5 * abs(o.deposit)
 
 
+@pytest.mark.parametrize("A,vs", workloads.MAIN_2D_SWEEP)
+def test_fp32_sweep_grid_before_saturation(A, vs):
+    # the buoyancy x settling-velocity grid of the 2048 x 4096 workload, on the small lattice
+    wl = workloads.SMALL_2D
+    c0 = wl.initial_c()
+    kw = dict(tau=wl.tau, gravity=A, density_contrast=1.0, settling_velocity=vs, diffusivity=wl.diffusivity)
+    g, o = _pair(wl.shape, c0, fp64=False, **kw)
+    g.step(300)
+    o.step(300)
+    _compare(g, o, 1e-5, 1e-5, 1e-6)
+    assert abs(g.deposit - o.deposit) <= 1e-5 * abs(o.deposit) + 1e-9
+
+
 @pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("shape", [(132, 40), (260, 70), (4, 8)])
 def test_fp32_ragged_shapes_frozen_velocity(shape, fused):
