@@ -539,7 +539,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
       return LW_ECUDA;
     }
   }
-  h->sweep3d = !h->fp64 && !variant && h->p.dim == 3 && !h->sugar && lw::sweep3d_supported(h->p.nz, h->walls);
+  h->sweep3d = !h->fp64 && !variant && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
   if (h->sweep3d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;

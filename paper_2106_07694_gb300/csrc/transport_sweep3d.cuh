@@ -45,7 +45,7 @@ struct Sweep3dParams {
   float ghost_shift; // 2 Vs / alpha
 };
 
-template <int STAGE>
+template <int STAGE, bool SUGAR = false>
 __global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, Sweep3dParams sp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sweep3dSmem& S = *reinterpret_cast<Sweep3dSmem*>(smem_raw);
@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, 
     const unsigned k = (unsigned)lr * plane + col;
     qc = __ldg(cin + k);
     const float u = __ldg(uz + k);
-    qw = fmaf(ghost ? -u : u, inv_alpha, -vs_a);
+    // with sugar the settling velocity of the node (a ghost reads its mirror's) is Vs (1 - ks S)
+    const float vsa = SUGAR ? vs_a * fmaf(-a.ks, __ldg(a.S + k), 1.f) : vs_a;
+    qw = fmaf(ghost ? -u : u, inv_alpha, -vsa);
   };
   auto col_put = [&](int l) {
     const float h = 0.5f * qc;
@@ -195,7 +197,8 @@ __global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, 
 
     // ---- divergence and the Shu-Osher combination of this stage
     if (!prime) {
-      const float fdn = k == 0 ? -a.vs * chere : carry;
+      const float vs_floor = SUGAR && k == 0 ? a.vs * fmaf(-a.ks, __ldg(a.S + col), 1.f) : a.vs;
+      const float fdn = k == 0 ? -vs_floor * chere : carry;
       const float L = S.fx[ty][tx] - S.fx[ty][tx + 1] + S.fy[ty][tx] - S.fy[ty + 1][tx] + fdn - fup;
       if (out) {
         const unsigned node = lv + col;
@@ -222,9 +225,13 @@ inline bool sweep3d_supported(int nz, bool walls) { return walls && nz >= 4; }
 
 inline cudaError_t sweep3d_prepare() {
   const int b = (int)sizeof(Sweep3dSmem);
-  cudaError_t e = cudaFuncSetAttribute(rk_sweep3d_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(rk_sweep3d_kernel<1>, at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<2>, at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<3>, at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<1, true>, at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<2, true>, at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<3, true>, at, b);
   return e;
 }
 
@@ -246,7 +253,10 @@ inline cudaError_t launch_sweep3d(const Args<float>& a, const float* cin, float*
   sp.H = H;
   sp.ghost_shift = 2.f * a.vs * a.inv_alpha;
   const dim3 grid((a.nx + kT3x - 1) / kT3x, (a.ny + kT3y - 1) / kT3y, (a.nz + H - 1) / H);
-  rk_sweep3d_kernel<STAGE><<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
+  if (a.S)
+    rk_sweep3d_kernel<STAGE, true><<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
+  else
+    rk_sweep3d_kernel<STAGE><<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
   return cudaGetLastError();
 }
 
