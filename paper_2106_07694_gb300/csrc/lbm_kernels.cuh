@@ -163,43 +163,61 @@ __global__ void __launch_bounds__(128) lbm_d2q9_record_kernel(Args<T> a, T* rho_
   lbm_d2q9_body<T, PARITY, true>(a, blockIdx.x, blockIdx.y, rho_out);
 }
 
-// Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.
-template <typename T, int PARITY, bool RHO, bool SUGAR>
-__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out) {
-  const int x = bx * blockDim.x + threadIdx.x;
-  const int y = by;
-  const int nx = a.nx, ny = a.ny;
-  if (x >= nx) return;
-  const unsigned n = (unsigned)a.n;
-  const unsigned node = (unsigned)y * (unsigned)nx + (unsigned)x;
-  const bool walls = a.walls != 0;
-  // neighbour offsets relative to node along x and y (periodic x; y periodic or walled)
-  const int dxm = x == 0 ? nx - 1 : -1;          // offset of x-1
-  const int dxp = x == nx - 1 ? -(nx - 1) : 1;   // offset of x+1
-  const bool bot = y == 0, top = y == ny - 1;
-  const int dym = bot ? (walls ? 0 : (ny - 1) * nx) : -nx;  // offset of y-1 (0: wall)
-  const int dyp = top ? (walls ? 0 : -(ny - 1) * nx) : nx;  // offset of y+1 (0: wall)
-  const bool wall_m = walls && bot, wall_p = walls && top;
-  T* __restrict__ G = a.g;
-  auto off = [&](int i, int s) -> int {  // offset of node + s*c_i (s = +-1), without the wall test
+// One D2Q9 node's neighbour offsets along x and y (periodic x; y periodic or walled) and
+// its wall flags.
+struct D2Q9Node {
+  unsigned node;
+  int dxm, dxp, dym, dyp;  // offsets of x-1, x+1, y-1, y+1 (0 behind a wall)
+  bool wall_m, wall_p;     // floor below / lid above
+  __device__ __forceinline__ int off(int i, int s) const {  // node + s c_i, without the wall test
     const int cx = s * D2Q9::cx(i), cy = s * D2Q9::cy(i);
     return (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) + (cy > 0 ? dyp : (cy < 0 ? dym : 0));
-  };
-  auto behind_wall = [&](int i, int s) -> bool {
+  }
+  __device__ __forceinline__ bool behind_wall(int i, int s) const {
     const int cy = s * D2Q9::cy(i);
     return (cy < 0 && wall_m) || (cy > 0 && wall_p);
-  };
+  }
+};
 
-  T g[9];
+template <typename T>
+__device__ __forceinline__ D2Q9Node d2q9_node(const Args<T>& a, int x, int y) {
+  const int nx = a.nx, ny = a.ny;
+  const bool walls = a.walls != 0;
+  D2Q9Node nd;
+  nd.node = (unsigned)y * (unsigned)nx + (unsigned)x;
+  nd.dxm = x == 0 ? nx - 1 : -1;
+  nd.dxp = x == nx - 1 ? -(nx - 1) : 1;
+  const bool bot = y == 0, top = y == ny - 1;
+  nd.dym = bot ? (walls ? 0 : (ny - 1) * nx) : -nx;
+  nd.dyp = top ? (walls ? 0 : -(ny - 1) * nx) : nx;
+  nd.wall_m = walls && bot;
+  nd.wall_p = walls && top;
+  return nd;
+}
+
+// The node's populations as they stand at the start of a step of this parity (AA pattern).
+template <typename T, int PARITY>
+__device__ __forceinline__ void d2q9_load(const Args<T>& a, const D2Q9Node& nd, T (&g)[9]) {
+  const unsigned n = (unsigned)a.n;
+  const T* __restrict__ G = a.g;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     if (PARITY == 0) {
-      g[i] = __ldcs(G + i * n + node);
+      g[i] = __ldcs(G + i * n + nd.node);
     } else {
-      g[i] = behind_wall(i, -1) ? __ldcs(G + i * n + node)
-                                : __ldcs(G + D2Q9::opp(i) * n + (unsigned)((int)node + off(i, -1)));
+      g[i] = nd.behind_wall(i, -1) ? __ldcs(G + i * n + nd.node)
+                                   : __ldcs(G + D2Q9::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
     }
   }
+}
+
+// Moments, BGK-Guo collision and the in-place AA store of one node.
+template <typename T, int PARITY, bool RHO, bool SUGAR>
+__device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9Node& nd, const T (&g)[9],
+                                                   T* rho_out) {
+  const unsigned n = (unsigned)a.n;
+  const unsigned node = nd.node;
+  T* __restrict__ G = a.g;
   T drho = T(0), jx = T(0), jy = T(0);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -224,10 +242,10 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, 
     if (PARITY == 0) {
       __stcs(G + D2Q9::opp(i) * n + node, gs);
     } else {
-      if (behind_wall(i, +1))
+      if (nd.behind_wall(i, +1))
         __stcs(G + D2Q9::opp(i) * n + node, gs);
       else
-        __stcs(G + i * n + (unsigned)((int)node + off(i, +1)), gs);
+        __stcs(G + i * n + (unsigned)((int)node + nd.off(i, +1)), gs);
     }
   };
   // rest population
@@ -251,6 +269,17 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, 
     store(i, keep * g[i] + om * (even + odd) + (seven + sodd));
     store(i + 1, keep * g[i + 1] + om * (even - odd) + (seven - sodd));
   }
+}
+
+// Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.
+template <typename T, int PARITY, bool RHO, bool SUGAR>
+__device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out) {
+  const int x = bx * blockDim.x + threadIdx.x;
+  if (x >= a.nx) return;
+  const D2Q9Node nd = d2q9_node(a, x, by);
+  T g[9];
+  d2q9_load<T, PARITY>(a, nd, g);
+  d2q9_collide_store<T, PARITY, RHO, SUGAR>(a, nd, g, rho_out);
 }
 
 // D3Q19 specialisation (same arithmetic as lbm_step_kernel): 32-bit offsets with the
