@@ -286,42 +286,62 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, 
 // neighbour offsets along x, y (periodic) and z (walls or periodic) hoisted, the wall
 // tests taken once per block (a block is one x segment of one (y, z) row), streaming
 // cache hints on the population traffic.
-template <typename T, int PARITY, bool SUGAR = false>
-__global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  if (x >= nx) return;
-  const unsigned n = (unsigned)a.n;
-  const int plane = nx * ny;
-  const unsigned node = (unsigned)z * (unsigned)plane + (unsigned)y * (unsigned)nx + (unsigned)x;
-  const bool walls = a.walls != 0;
-  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? -(nx - 1) : 1;
-  const int dym = y == 0 ? (ny - 1) * nx : -nx, dyp = y == ny - 1 ? -(ny - 1) * nx : nx;
-  const bool bot = z == 0, top = z == nz - 1;
-  const int dzm = bot ? (walls ? 0 : (nz - 1) * plane) : -plane;
-  const int dzp = top ? (walls ? 0 : -(nz - 1) * plane) : plane;
-  const bool wall_m = walls && bot, wall_p = walls && top;
-  T* __restrict__ G = a.g;
-  auto off = [&](int i, int s) -> int {
+// One D3Q19 node's neighbour offsets (periodic x and y; z periodic or walled) and wall
+// flags.
+struct D3Q19Node {
+  unsigned node;
+  int dxm, dxp, dym, dyp, dzm, dzp;  // offsets of the six face neighbours (0 behind a wall)
+  bool wall_m, wall_p;               // floor below / lid above
+  __device__ __forceinline__ int off(int i, int s) const {  // node + s c_i, without the wall test
     const int cx = s * D3Q19::cx(i), cy = s * D3Q19::cy(i), cz = s * D3Q19::cz(i);
     return (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) +
            (cz > 0 ? dzp : (cz < 0 ? dzm : 0));
-  };
-  auto behind_wall = [&](int i, int s) -> bool {
+  }
+  __device__ __forceinline__ bool behind_wall(int i, int s) const {
     const int cz = s * D3Q19::cz(i);
     return (cz < 0 && wall_m) || (cz > 0 && wall_p);
-  };
-  T g[19];
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ D3Q19Node d3q19_node(const Args<T>& a, int x, int y, int z) {
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int plane = nx * ny;
+  const bool walls = a.walls != 0;
+  D3Q19Node nd;
+  nd.node = (unsigned)z * (unsigned)plane + (unsigned)y * (unsigned)nx + (unsigned)x;
+  nd.dxm = x == 0 ? nx - 1 : -1;
+  nd.dxp = x == nx - 1 ? -(nx - 1) : 1;
+  nd.dym = y == 0 ? (ny - 1) * nx : -nx;
+  nd.dyp = y == ny - 1 ? -(ny - 1) * nx : nx;
+  const bool bot = z == 0, top = z == nz - 1;
+  nd.dzm = bot ? (walls ? 0 : (nz - 1) * plane) : -plane;
+  nd.dzp = top ? (walls ? 0 : -(nz - 1) * plane) : plane;
+  nd.wall_m = walls && bot;
+  nd.wall_p = walls && top;
+  return nd;
+}
+
+template <typename T, int PARITY>
+__device__ __forceinline__ void d3q19_load(const Args<T>& a, const D3Q19Node& nd, T (&g)[19]) {
+  const unsigned n = (unsigned)a.n;
+  const T* __restrict__ G = a.g;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     if (PARITY == 0) {
-      g[i] = __ldcs(G + i * n + node);
+      g[i] = __ldcs(G + i * n + nd.node);
     } else {
-      g[i] = behind_wall(i, -1) ? __ldcs(G + i * n + node)
-                                : __ldcs(G + D3Q19::opp(i) * n + (unsigned)((int)node + off(i, -1)));
+      g[i] = nd.behind_wall(i, -1) ? __ldcs(G + i * n + nd.node)
+                                   : __ldcs(G + D3Q19::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
     }
   }
+}
+
+template <typename T, int PARITY, bool SUGAR>
+__device__ __forceinline__ void d3q19_collide_store(const Args<T>& a, const D3Q19Node& nd, const T (&g)[19]) {
+  const unsigned n = (unsigned)a.n;
+  const unsigned node = nd.node;
+  T* __restrict__ G = a.g;
   T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
@@ -348,10 +368,10 @@ __global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
     if (PARITY == 0) {
       __stcs(G + D3Q19::opp(i) * n + node, gs);
     } else {
-      if (behind_wall(i, +1))
+      if (nd.behind_wall(i, +1))
         __stcs(G + D3Q19::opp(i) * n + node, gs);
       else
-        __stcs(G + i * n + (unsigned)((int)node + off(i, +1)), gs);
+        __stcs(G + i * n + (unsigned)((int)node + nd.off(i, +1)), gs);
     }
   };
   {
@@ -372,6 +392,16 @@ __global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
     store(i, keep * g[i] + om * (even + odd) + (seven + sodd));
     store(i + 1, keep * g[i + 1] + om * (even - odd) + (seven - sodd));
   }
+}
+
+template <typename T, int PARITY, bool SUGAR = false>
+__global__ void __launch_bounds__(128) lbm_d3q19_kernel(Args<T> a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.nx) return;
+  const D3Q19Node nd = d3q19_node(a, x, blockIdx.y, blockIdx.z);
+  T g[19];
+  d3q19_load<T, PARITY>(a, nd, g);
+  d3q19_collide_store<T, PARITY, SUGAR>(a, nd, g);
 }
 
 // Macroscopic fields of the current state (parity as in load_populations):
