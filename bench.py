@@ -126,7 +126,7 @@ class ClockSampler:
 # taken on; a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
     "rk3_sweep2d": (127.72e6, "paper_2106_07694_gb300/csrc/transport_sweep2d.cuh", "83e0464e30c5"),
-    "lbm_collide_stream": (643.99e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "3d0cf7d72c36"),
+    "lbm_collide_stream": (645.42e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "730ac8bff4cd"),
     "rk_stage1": (112.73e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
     "rk_stage2": (150.98e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
     "rk_stage3": (146.65e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),

@@ -45,8 +45,8 @@ struct Sweep3dParams {
   float ghost_shift; // 2 Vs / alpha
 };
 
-template <int STAGE, bool SUGAR = false>
-__global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, Sweep3dParams sp) {
+template <int STAGE, bool SUGAR>
+__device__ __forceinline__ void rk_sweep3d_body(const Args<float>& a, const Sweep3dParams& sp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sweep3dSmem& S = *reinterpret_cast<Sweep3dSmem*>(smem_raw);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kT3x + tx;
@@ -219,6 +219,31 @@ __global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, 
   }
 }
 
+// Two entry points with the same body: uncapped (57-62 registers for stages 1 and 2), and
+// capped at 64 registers (four resident 256-thread CTAs per SM) for the instantiations the
+// compiler would otherwise give more (stage 3: 72; stage 1 with sugar).  An explicit
+// minimum of one block is not the same as none: it lets stages 1 and 2 grow to 72.
+template <int STAGE, bool SUGAR = false>
+__global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, Sweep3dParams sp) {
+  rk_sweep3d_body<STAGE, SUGAR>(a, sp);
+}
+
+template <int STAGE, bool SUGAR = false>
+__global__ void __launch_bounds__(kT3x * kT3y, 4) rk_sweep3d_capped_kernel(Args<float> a, Sweep3dParams sp) {
+  rk_sweep3d_body<STAGE, SUGAR>(a, sp);
+}
+
+template <int STAGE, bool SUGAR>
+constexpr bool sweep3d_capped() { return (STAGE == 3 && !SUGAR) || (STAGE == 1 && SUGAR); }
+
+template <int STAGE, bool SUGAR>
+inline void (*sweep3d_entry())(Args<float>, Sweep3dParams) {
+  if constexpr (sweep3d_capped<STAGE, SUGAR>())
+    return rk_sweep3d_capped_kernel<STAGE, SUGAR>;
+  else
+    return rk_sweep3d_kernel<STAGE, SUGAR>;
+}
+
 inline size_t sweep3d_smem() { return sizeof(Sweep3dSmem); }
 
 inline bool sweep3d_supported(int nz, bool walls) { return walls && nz >= 4; }
@@ -226,12 +251,12 @@ inline bool sweep3d_supported(int nz, bool walls) { return walls && nz >= 4; }
 inline cudaError_t sweep3d_prepare() {
   const int b = (int)sizeof(Sweep3dSmem);
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(rk_sweep3d_kernel<1>, at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<2>, at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<3>, at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<1, true>, at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<2, true>, at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk_sweep3d_kernel<3, true>, at, b);
+  cudaError_t e = cudaFuncSetAttribute(sweep3d_entry<1, false>(), at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<2, false>(), at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<3, false>(), at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<1, true>(), at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<2, true>(), at, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<3, true>(), at, b);
   return e;
 }
 
@@ -254,9 +279,9 @@ inline cudaError_t launch_sweep3d(const Args<float>& a, const float* cin, float*
   sp.ghost_shift = 2.f * a.vs * a.inv_alpha;
   const dim3 grid((a.nx + kT3x - 1) / kT3x, (a.ny + kT3y - 1) / kT3y, (a.nz + H - 1) / H);
   if (a.S)
-    rk_sweep3d_kernel<STAGE, true><<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
+    sweep3d_entry<STAGE, true>()<<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
   else
-    rk_sweep3d_kernel<STAGE><<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
+    sweep3d_entry<STAGE, false>()<<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
   return cudaGetLastError();
 }
 
