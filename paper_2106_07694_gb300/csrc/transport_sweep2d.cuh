@@ -40,23 +40,28 @@ namespace lw {
 //   beta_0 = 13/12 (d2-d1)^2 + 1/4 (3 d2 - d1)^2,  beta_1 = 13/12 (d3-d2)^2 + 1/4 (d2+d3)^2,
 //   beta_2 = 13/12 (d4-d3)^2 + 1/4 (d4 - 3 d3)^2;
 //   6 (q_k - c) = 5 d2 - 2 d1,  d2 + 2 d3,  4 d3 - d4;
-// and one division: with A_k = (eps + beta_k)^2 the weights are proportional to
-// d_k prod_{j != k} A_j.  Returns the face value c + sum_k w_k (q_k - c).
+// and one division.  The weights are proportional to d_k prod_{j != k} A_j with
+// A_k = (eps + beta_k)^2, and only their ratios matter, so beta_k and eps are both scaled
+// by 12/13 (beta_k' = s_k^2 + 3/13 t_k^2) and the linear weights (1, 6, 3)/10 by 10:
+//   q-weights  A1 A2,  6 A0 A2,  3 A0 A1;
+//   numerator  A1 (A2 r0 + 3 A0 r2) + 6 A0 A2 r1,  denominator  A1 (A2 + 3 A0) + 6 A0 A2.
+// Returns the face value c + sum_k w_k (q_k - c).
 __device__ __forceinline__ float weno5_face_value(float a, float b, float c, float d, float e) {
   const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
   const float s0 = d2 - d1, s1 = d3 - d2, s2 = d4 - d3;
   const float t0 = fmaf(3.f, d2, -d1), t1 = d2 + d3, t2 = fmaf(-3.f, d3, d4);
-  const float k = 13.f / 12.f, eps = 1e-6f;
-  float A0 = fmaf(k * s0, s0, fmaf(0.25f * t0, t0, eps));
-  float A1 = fmaf(k * s1, s1, fmaf(0.25f * t1, t1, eps));
-  float A2 = fmaf(k * s2, s2, fmaf(0.25f * t2, t2, eps));
+  const float q = 3.f / 13.f, eps = 1e-6f * (12.f / 13.f);
+  float A0 = fmaf(s0, s0, fmaf(q * t0, t0, eps));
+  float A1 = fmaf(s1, s1, fmaf(q * t1, t1, eps));
+  float A2 = fmaf(s2, s2, fmaf(q * t2, t2, eps));
   A0 *= A0;
   A1 *= A1;
   A2 *= A2;
-  const float p0 = 0.1f * (A1 * A2), p1 = 0.6f * (A0 * A2), p2 = 0.3f * (A0 * A1);
   const float r0 = fmaf(5.f, d2, -2.f * d1), r1 = fmaf(2.f, d3, d2), r2 = fmaf(4.f, d3, -d4);
-  const float num = fmaf(p2, r2, fmaf(p1, r1, p0 * r0));
-  return c + __fdividef(num, 6.f * ((p0 + p1) + p2));
+  const float A02x6 = 6.f * (A0 * A2);
+  const float num = fmaf(A1, fmaf(3.f * A0, r2, A2 * r0), A02x6 * r1);
+  const float den = fmaf(A1, fmaf(3.f, A0, A2), A02x6);
+  return fmaf(__fdividef(num, den), 1.f / 6.f, c);
 }
 
 // Total face flux (unscaled): alpha (h+ + h-) + kappa (cl - cr), with h+ from the
