@@ -122,27 +122,37 @@ class ClockSampler:
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/, with the SHA-1 prefix of the kernel source they were
-# taken on; a changed kernel reports null until it is captured again.
+# captures summarised in profiles/, with the SHA-1 prefix of the kernel sources they were
+# taken on (the kernel's file and the headers it includes, concatenated in this order); a
+# changed kernel reports null until it is captured again.
+_CSRC = "paper_2106_07694_gb300/csrc/"
+_LBM_SRC = ("lbm_kernels.cuh", "lattice.cuh", "common.cuh")
+_STAGE_SRC = ("transport_stage2d.cuh", "transport_sweep2d.cuh", "reduce_kernels.cuh", "common.cuh")
 NCU_TRAFFIC = {
-    "rk3_sweep2d": (127.72e6, "paper_2106_07694_gb300/csrc/transport_sweep2d.cuh", "83e0464e30c5"),
-    "lbm_collide_stream": (645.42e6, "paper_2106_07694_gb300/csrc/lbm_kernels.cuh", "730ac8bff4cd"),
-    "rk_stage1": (112.73e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
-    "rk_stage2": (150.98e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
-    "rk_stage3": (146.65e6, "paper_2106_07694_gb300/csrc/transport_stage2d.cuh", "f36fff083293"),
+    "lbm_collide_stream": (644.09e6, _LBM_SRC, "294f01f82826"),
+    "rk_stage1": (113.04e6, _STAGE_SRC, "57d585a4f7d3"),
+    "rk_stage2": (153.85e6, _STAGE_SRC, "57d585a4f7d3"),
+    "rk_stage3": (146.68e6, _STAGE_SRC, "57d585a4f7d3"),
     # 512 x 1024 adjoint workload (the face records stay in L2)
-    "adj_faces": (9.12e6, "paper_2106_07694_gb300/csrc/adjoint.cuh", "bb59bd120597"),
+    "adj_faces": (8.62e6, ("adjoint.cuh",) + _LBM_SRC, "9c7993dd6b7b"),
 }
 
 
-def kernel_traffic(name):
+def source_hash(files):
     import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, _CSRC + f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def kernel_traffic(name):
     if name not in NCU_TRAFFIC:
         return None
-    nbytes, src, sha = NCU_TRAFFIC[name]
+    nbytes, files, sha = NCU_TRAFFIC[name]
     try:
-        with open(os.path.join(ROOT, src), "rb") as fh:
-            cur = hashlib.sha1(fh.read()).hexdigest()[:12]
+        cur = source_hash(files)
     except OSError:
         return None
     return nbytes if cur == sha else None
@@ -574,7 +584,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=0, help="override the horizon (profiling only)")
     ap.add_argument("--adjoint-segment", type=int, default=0, help="override the checkpoint spacing")
