@@ -6,8 +6,10 @@
 // in shared memory (prefetched one row ahead), computes the left x face of every column
 // (the strip's right edge face by one lane of warp 0), and the upper y face of its own
 // column from a ring of y-split fluxes running three rows ahead; the lower y face is
-// carried from the previous row.  Every face of the stage is computed once.  Small
-// shared-memory footprint (about 14 KB), so many CTAs share an SM.  Three launches make
+// carried from the previous row.  Every face of the stage is computed once.  The ring
+// holds six rows, each stored twice (slots r and r + 6), so a face reads its six rows
+// from one base slot without wrap-around arithmetic.  Small shared-memory footprint
+// (about 21 KB), so many CTAs share an SM.  Three launches make
 // a step (the stage-3 kernel also folds the floor deposit); c1 and c2 go through L2/HBM.
 #pragma once
 #include "common.cuh"
@@ -18,15 +20,15 @@ namespace lw {
 constexpr int kS2T = 128;             // columns per CTA (threads)
 constexpr int kS2h = 3;               // stencil radius
 constexpr int kS2X = kS2T + 2 * kS2h;
-constexpr int kS2r = 8;               // y ring depth
+constexpr int kS2r = 6;               // y ring depth (rows k-2 .. k+3), stored twice
 
 struct Stage2dSmem {
   float xp[kS2X];  // x-split h+/alpha of the current row (strip + halo)
   float xm[kS2X];
   float c[kS2X];   // stage input value of the current row
-  float yp[kS2r][kS2T];  // y-split ring of each column
-  float ym[kS2r][kS2T];
-  float cy[kS2r][kS2T];  // stage input value ring of each column
+  float yp[2 * kS2r][kS2T];  // y-split ring of each column; slot r and r + 6 hold the same
+  float ym[2 * kS2r][kS2T];  // row, so the six rows of a face are read without wrap-around
+  float cy[2 * kS2r][kS2T];  // stage input value ring of each column, stored the same way
   float fx[kS2T + 1];    // left x faces (+ right edge)
 };
 
@@ -81,11 +83,14 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     const float vsa = SUGAR ? vs_a * fmaf(-a.ks, __ldg(a.S + k), 1.f) : vs_a;
     qw = fmaf(ghost ? -u : u, inv_alpha, -vsa);
   };
-  auto col_put = [&](int l) {
-    const float h = 0.5f * qc;
-    S.yp[l & (kS2r - 1)][t] = fmaf(qw, h, h);
-    S.ym[l & (kS2r - 1)][t] = fmaf(qw, h, -h);
-    S.cy[l & (kS2r - 1)][t] = qc;
+  auto col_put = [&](int slot) {
+    const float h = 0.5f * qc, p = fmaf(qw, h, h), m = fmaf(qw, h, -h);
+    S.yp[slot][t] = p;
+    S.yp[slot + kS2r][t] = p;
+    S.ym[slot][t] = m;
+    S.ym[slot + kS2r][t] = m;
+    S.cy[slot][t] = qc;
+    S.cy[slot + kS2r][t] = qc;
   };
   auto cn_fetch = [&](int k) {
     if (STAGE > 1 && k < y1) qn = a.c[(unsigned)k * (unsigned)nx + X];
@@ -94,9 +99,10 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
   const int kb = y0 == 0 ? 0 : y0 - 1;  // first row: y0, or the priming row below it
   for (int l = kb - 2; l < kb + 3; ++l) {
     col_fetch(l);
-    col_put(l);
+    col_put(((l % kS2r) + kS2r) % kS2r);
   }
   col_fetch(kb + 3);
+  int slot = (kb + 3) % kS2r;  // ring slot of row k + 3
   fetch_row(kb);
   cn_fetch(kb);
   float carry = 0.f;
@@ -118,7 +124,7 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
       }
     }
     fetch_row(k + 1);
-    col_put(k + 3);
+    col_put(slot);
     col_fetch(k + 4);
     const float cn_here = qn;
     cn_fetch(k + 1);
@@ -134,13 +140,14 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
                               S.xm[e + 3], S.xm[e + 2], S.xm[e + 1], alpha, kappa, S.c[e + kS2h - 1], S.c[e + kS2h]);
       }
     }
-    const float chere = S.cy[k & (kS2r - 1)][t];
+    const int rb = slot == kS2r - 1 ? 0 : slot + 1;  // ring slot of row k - 2 (= that of row k + 4)
+    const float chere = S.cy[rb + 2][t], cnext = S.cy[rb + 3][t];
     float fup = 0.f;
     if (k != ny - 1) {
-      fup = face_flux_x(S.yp[(k - 2) & (kS2r - 1)][t], S.yp[(k - 1) & (kS2r - 1)][t], S.yp[k & (kS2r - 1)][t],
-                        S.yp[(k + 1) & (kS2r - 1)][t], S.yp[(k + 2) & (kS2r - 1)][t], S.ym[(k + 3) & (kS2r - 1)][t],
-                        S.ym[(k + 2) & (kS2r - 1)][t], S.ym[(k + 1) & (kS2r - 1)][t], S.ym[k & (kS2r - 1)][t],
-                        S.ym[(k - 1) & (kS2r - 1)][t], alpha, kappa, chere, S.cy[(k + 1) & (kS2r - 1)][t]);
+      const float* P = &S.yp[rb][t];
+      const float* M = &S.ym[rb][t];
+      fup = face_flux_x(P[0], P[kS2T], P[2 * kS2T], P[3 * kS2T], P[4 * kS2T], M[5 * kS2T], M[4 * kS2T],
+                        M[3 * kS2T], M[2 * kS2T], M[kS2T], alpha, kappa, chere, cnext);
     }
     __syncthreads();
 
@@ -170,6 +177,7 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
       }
     }
     carry = fup;
+    slot = rb;
   }
 
   // stage 3: the CTAs holding the floor row fold the deposit of this step (FP64,
