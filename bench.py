@@ -33,6 +33,11 @@ WORKLOADS = {
               "D2Q9"),
     "small": (workloads.SMALL_2D, "coupled LBM+WENO5 GLUPS (2D D2Q9 128x256 FP64, L2-resident parity case)",
               "D2Q9"),
+    "weno3": (workloads.WENO3_2D, "coupled LBM+WENO3 GLUPS (2D D2Q9 2048x4096 FP32, paper-literal WENO3)", "D2Q9"),
+    "signsplit": (workloads.SIGN_SPLIT_2D,
+                  "coupled LBM+WENO5 GLUPS (2D D2Q9 2048x4096 FP32, sign-upwind stencil choice)", "D2Q9"),
+    "classes": (workloads.CLASSES_2D,
+                "coupled LBM+WENO5 GLUPS (2D D2Q9 2048x4096 FP32, three particle classes)", "D2Q9"),
 }
 WL, METRIC, LATTICE = WORKLOADS["2d"]
 ADJOINT_METRIC = ("gradient of the deposited mass wrt c0 and Vs, GLUPS of the reverse-mode pass "
@@ -56,8 +61,17 @@ def fp32_peak_tflops(clk):
 
 
 def phys_kwargs(wl):
-    return dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
-                settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity, **wl.sugar)
+    kw = dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
+              settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity, **wl.sugar, **wl.scheme)
+    if wl.class_vs:
+        kw["class_vs"] = wl.class_vs
+    return kw
+
+
+def set_classes(sim, wl, to=lambda a: a):
+    """Class fields of a polydisperse workload (after init, which puts c0 in class 0)."""
+    for k, ck in enumerate(wl.initial_classes() if wl.class_vs else []):
+        sim.set_class(k, to(ck))
 
 
 def load_peaks():
@@ -169,6 +183,7 @@ def run_oracle_sample(wl, steps, threads):
     s.init(wl.initial_c())
     if wl.sugar:
         s.set_sugar(wl.initial_S())
+    set_classes(s, wl)
     s.step(1)
     t0 = time.perf_counter()
     s.step(steps)
@@ -192,6 +207,7 @@ def bench_reference(args):
     s.init(band.initial_c())
     if band.sugar:
         s.set_sugar(band.initial_S())
+    set_classes(s, band)
     s.step(args.warmup)
     t0 = time.perf_counter()
     s.step(args.steps)
@@ -242,6 +258,7 @@ def bench_ours(args):
     sim.init(torch.from_numpy(c0).to(dev))
     if S0 is not None:
         sim.set_sugar(torch.from_numpy(S0).to(dev))
+    set_classes(sim, wl, lambda a: torch.from_numpy(a.astype(np_dt)).to(dev))
     sim.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -291,6 +308,15 @@ def bench_ours(args):
     lbm_B = 2 * (9 if dim == 2 else 19) * es + es + (es if wl.sugar else 0)  # + S in (sugar force)
     step_B = lbm_B + es + (es if wl.sugar else 0)                               # + c out (+ S out)
     tr_flop = 915.0 if dim == 2 else 1371.0
+    # scheme variants, same count on their own formulation: WENO3 21 flop per reconstruction
+    # (two candidates, two indicators, weights, normalisation, combination) -> 327 flop; the
+    # sign-upwind choice one WENO5 reconstruction per face (+ face velocity) -> 477 flop
+    if wl.scheme.get("weno3"):
+        tr_flop = 327.0
+    elif wl.scheme.get("sign_split"):
+        tr_flop = 477.0
+    ncls = max(1, len(wl.class_vs))
+    step_B += 2 * es * (ncls - 1)  # every class's c in and out
     flop_of = {"rk3_sweep2d": tr_flop, "rk3_sweep3d": tr_flop, "rk_stage1": tr_flop / 3,
                "rk_stage2": tr_flop / 3, "rk_stage3": tr_flop / 3}
     sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
@@ -333,7 +359,9 @@ def bench_ours(args):
         a_ = tr_flop * wl.nodes / t_tr / 1e12
         transport_roofline = {"bound": "alu", "kernels": tr_kernels, "achieved": a_, "peak": fp32_peak,
                               "unit": "TFLOP/s", "frac": a_ / fp32_peak, "alg_flop_per_node": tr_flop,
-                              "us_per_step": t_tr * 1e6}
+                              "us_per_step": t_tr * 1e6 * ncls}
+        if ncls > 1:
+            transport_roofline["note"] = f"per class; the three stage kernels run once per class ({ncls})"
     step_roofline = {"bound": "hbm", "alg_bytes_per_node": step_B,
                      "achieved": step_B * wl.nodes / (step_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": step_B * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
@@ -343,10 +371,13 @@ def bench_ours(args):
     c_host = torch.from_numpy(c0).pin_memory()
     c_out = torch.empty_like(c_host).pin_memory()
     S_host = torch.from_numpy(S0).pin_memory() if S0 is not None else None
+    cls_host = [torch.from_numpy(a.astype(np_dt)).pin_memory() for a in wl.initial_classes()] if wl.class_vs else []
     sim2 = lw.Simulation(wl.shape, fp64=fp64, stream=stream, **kw)
     sim2.init(c_host)
     if S_host is not None:
         sim2.set_sugar(S_host)
+    for k, ck in enumerate(cls_host):
+        sim2.set_class(k, ck)
     sim2.step(1)
     torch.cuda.synchronize()
     barrier()
@@ -354,6 +385,8 @@ def bench_ours(args):
     sim2.init(c_host)
     if S_host is not None:
         sim2.set_sugar(S_host)
+    for k, ck in enumerate(cls_host):
+        sim2.set_class(k, ck)
     sim2.step(args.steps)
     dep = sim2.deposit
     lw.lbm_wenoc_fields(sim2.handle, None, None, c_out)
@@ -361,8 +394,8 @@ def bench_ours(args):
     barrier()
     e2e_s = job_time_ms(e2e_s * 1e3, device=dev) * 1e-3
     e2e = {"value": world * wl.nodes * args.steps / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": (c_host.numel() * c_host.element_size() * (2 if S_host is not None else 1))
-           / args.steps,
+           "h2d_bytes_per_step": (c_host.numel() * c_host.element_size() * (2 if S_host is not None else 1)
+                                  + sum(t.numel() * t.element_size() for t in cls_host)) / args.steps,
            "d2h_bytes_per_step": (c_out.numel() * c_out.element_size() + 8) / args.steps,
            "note": "per job: H2D c0 (+ S0) + init + K steps + deposit (8 B) + D2H c, host wall clock"}
     assert np.isfinite(dep)
@@ -385,6 +418,8 @@ def bench_ours(args):
             "config": {"workload": wl.name, "shape": list(wl.shape), "lattice": LATTICE,
                        "tau": wl.tau, "A": wl.gravity * wl.density_contrast, "Vs": wl.settling_velocity,
                        "kappa": wl.diffusivity, "parallelism": f"replicas{world}", **({"sugar": wl.sugar} if wl.sugar else {}),
+                       **({"scheme": wl.scheme} if wl.scheme else {}),
+                       **({"class_vs": list(wl.class_vs)} if wl.class_vs else {}),
                        "l2": (lambda mb: f"inputs larger than L2 (populations {mb:.0f} MB)" if mb > 129
                               else f"inputs fit in L2 (populations {mb:.1f} MB): no L2 flush claim")(
                            wl.nodes * (9 if len(wl.shape) == 2 else 19) * (8 if fp64 else 4) / 1e6)},

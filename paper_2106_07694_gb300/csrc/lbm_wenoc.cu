@@ -509,7 +509,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   h->walls = (p->flags & LW_PERIODIC_VERTICAL) == 0;
   h->frozen = (p->flags & LW_FROZEN_VELOCITY) != 0;
   h->sugar = (p->flags & LW_SUGAR) != 0;
-  const bool variant = (p->flags & (LW_WENO3 | LW_SIGN_SPLIT)) != 0;  // generic stage kernels
+  const bool variant = (p->flags & (LW_WENO3 | LW_SIGN_SPLIT)) != 0;  // transport-scheme variant
   h->use_graphs = (p->flags & LW_NO_GRAPH) == 0;
   h->n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
   h->ncls = classes_of(*p);
@@ -522,7 +522,8 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   cudaGetDevice(&h->device);
   h->sweep = !h->fp64 && !variant && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
-  h->stage2d = !h->fp64 && !variant && h->p.dim == 2 && h->walls && !h->sweep &&
+  // the row-sweep stage kernels take the scheme variants too, except with the sugar scalar
+  h->stage2d = !h->fp64 && !(variant && h->sugar) && h->p.dim == 2 && h->walls && !h->sweep &&
                (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
   if (h->stage2d) {
     int sms = 0;
@@ -539,7 +540,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
       return LW_ECUDA;
     }
   }
-  h->sweep3d = !h->fp64 && !variant && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
+  h->sweep3d = !h->fp64 && !(variant && h->sugar) && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
   if (h->sweep3d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;

@@ -80,12 +80,19 @@ struct ClassPtrs {
   int count;
 };
 
+// The loads of every class are issued before the sums (unrolled to the 8-class maximum);
+// the sum runs in class order.
 template <typename T>
 __global__ void class_sum_kernel(ClassPtrs<T> cp, T* out, long long n) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  T acc = cp.c[0][k];
-  for (int m = 1; m < cp.count; ++m) acc += cp.c[m][k];
+  T v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = m < cp.count ? __ldg(cp.c[m] + k) : T(0);
+  T acc = v[0];
+#pragma unroll
+  for (int m = 1; m < 8; ++m)
+    if (m < cp.count) acc += v[m];
   out[k] = acc;
 }
 

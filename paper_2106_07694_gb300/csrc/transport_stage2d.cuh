@@ -39,8 +39,9 @@ struct Stage2dParams {
 };
 
 // Body of the stage kernel for strip bx, segment by; `strips` = number of strips (the
-// floor CTAs that fold the deposit).
-template <int STAGE, bool SUGAR = false>
+// floor CTAs that fold the deposit).  SCHEME: transport-scheme variant bits (kSchemeWeno3,
+// kSchemeSignSplit; 0 = Lax-Friedrichs WENO5), see face_flux_scheme.
+template <int STAGE, bool SUGAR = false, int SCHEME = 0>
 __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2dParams& sp, int bx, int by,
                                              int strips) {
   __shared__ __align__(16) Stage2dSmem S;
@@ -83,8 +84,9 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     const float vsa = SUGAR ? vs_a * fmaf(-a.ks, __ldg(a.S + k), 1.f) : vs_a;
     qw = fmaf(ghost ? -u : u, inv_alpha, -vsa);
   };
+  constexpr bool SIGN = (SCHEME & kSchemeSignSplit) != 0;
   auto col_put = [&](int slot) {
-    const float h = 0.5f * qc, p = fmaf(qw, h, h), m = fmaf(qw, h, -h);
+    const float h = 0.5f * qc, p = SIGN ? qw * qc : fmaf(qw, h, h), m = SIGN ? qw : fmaf(qw, h, -h);
     S.yp[slot][t] = p;
     S.yp[slot + kS2r][t] = p;
     S.ym[slot][t] = m;
@@ -114,13 +116,13 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     {
       const float h0 = 0.5f * p0c, w0 = p0u * inv_alpha;
       S.c[t] = p0c;
-      S.xp[t] = fmaf(w0, h0, h0);
-      S.xm[t] = fmaf(w0, h0, -h0);
+      S.xp[t] = SIGN ? w0 * p0c : fmaf(w0, h0, h0);
+      S.xm[t] = SIGN ? w0 : fmaf(w0, h0, -h0);
       if (has2) {
         const float h1 = 0.5f * p1c, w1 = p1u * inv_alpha;
         S.c[j1] = p1c;
-        S.xp[j1] = fmaf(w1, h1, h1);
-        S.xm[j1] = fmaf(w1, h1, -h1);
+        S.xp[j1] = SIGN ? w1 * p1c : fmaf(w1, h1, h1);
+        S.xm[j1] = SIGN ? w1 : fmaf(w1, h1, -h1);
       }
     }
     fetch_row(k + 1);
@@ -132,12 +134,28 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
 
     // ---- faces: left x face of this column (and the strip's right edge), upper y face
     if (!prime) {
-      S.fx[t] = face_flux_x(S.xp[t], S.xp[t + 1], S.xp[t + 2], S.xp[t + 3], S.xp[t + 4], S.xm[t + 5], S.xm[t + 4],
-                            S.xm[t + 3], S.xm[t + 2], S.xm[t + 1], alpha, kappa, S.c[t + kS2h - 1], S.c[t + kS2h]);
-      if (t == 0) {
-        const int e = kS2T;
-        S.fx[e] = face_flux_x(S.xp[e], S.xp[e + 1], S.xp[e + 2], S.xp[e + 3], S.xp[e + 4], S.xm[e + 5], S.xm[e + 4],
-                              S.xm[e + 3], S.xm[e + 2], S.xm[e + 1], alpha, kappa, S.c[e + kS2h - 1], S.c[e + kS2h]);
+      if constexpr (SCHEME == 0) {
+        S.fx[t] = face_flux_x(S.xp[t], S.xp[t + 1], S.xp[t + 2], S.xp[t + 3], S.xp[t + 4], S.xm[t + 5],
+                              S.xm[t + 4], S.xm[t + 3], S.xm[t + 2], S.xm[t + 1], alpha, kappa, S.c[t + kS2h - 1],
+                              S.c[t + kS2h]);
+        if (t == 0) {
+          const int e = kS2T;
+          S.fx[e] = face_flux_x(S.xp[e], S.xp[e + 1], S.xp[e + 2], S.xp[e + 3], S.xp[e + 4], S.xm[e + 5],
+                                S.xm[e + 4], S.xm[e + 3], S.xm[e + 2], S.xm[e + 1], alpha, kappa, S.c[e + kS2h - 1],
+                                S.c[e + kS2h]);
+        }
+      } else {
+        auto xface = [&](int j) {  // face between staging positions j + 2 and j + 3
+          float p[6], m[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            p[q] = S.xp[j + q];
+            m[q] = S.xm[j + q];
+          }
+          return face_flux_scheme<SCHEME>(p, m, alpha, kappa, S.c[j + kS2h - 1], S.c[j + kS2h]);
+        };
+        S.fx[t] = xface(t);
+        if (t == 0) S.fx[kS2T] = xface(kS2T);
       }
     }
     const int rb = slot == kS2r - 1 ? 0 : slot + 1;  // ring slot of row k - 2 (= that of row k + 4)
@@ -146,8 +164,18 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     if (k != ny - 1) {
       const float* P = &S.yp[rb][t];
       const float* M = &S.ym[rb][t];
-      fup = face_flux_x(P[0], P[kS2T], P[2 * kS2T], P[3 * kS2T], P[4 * kS2T], M[5 * kS2T], M[4 * kS2T],
-                        M[3 * kS2T], M[2 * kS2T], M[kS2T], alpha, kappa, chere, cnext);
+      if constexpr (SCHEME == 0) {
+        fup = face_flux_x(P[0], P[kS2T], P[2 * kS2T], P[3 * kS2T], P[4 * kS2T], M[5 * kS2T], M[4 * kS2T],
+                          M[3 * kS2T], M[2 * kS2T], M[kS2T], alpha, kappa, chere, cnext);
+      } else {
+        float p[6], m[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          p[q] = P[q * kS2T];
+          m[q] = M[q * kS2T];
+        }
+        fup = face_flux_scheme<SCHEME>(p, m, alpha, kappa, chere, cnext);
+      }
     }
     __syncthreads();
 
@@ -209,9 +237,9 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
   }
 }
 
-template <int STAGE, bool SUGAR = false>
+template <int STAGE, bool SUGAR = false, int SCHEME = 0>
 __global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2dParams sp) {
-  stage2d_body<STAGE, SUGAR>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
+  stage2d_body<STAGE, SUGAR, SCHEME>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
@@ -233,8 +261,15 @@ inline cudaError_t launch_stage2d(const Args<float>& a, const float* cin, float*
   sp.cout = cout;
   sp.H = H;
   const dim3 grid((a.nx + kS2T - 1) / kS2T, (a.ny + H - 1) / H);
+  // the scheme variants have no sugar instantiation (those handles take the generic path)
   if (a.S)
     rk_stage2d_kernel<STAGE, true><<<grid, kS2T, 0, s>>>(a, sp);
+  else if (a.scheme == kSchemeWeno3)
+    rk_stage2d_kernel<STAGE, false, kSchemeWeno3><<<grid, kS2T, 0, s>>>(a, sp);
+  else if (a.scheme == kSchemeSignSplit)
+    rk_stage2d_kernel<STAGE, false, kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
+  else if (a.scheme == (kSchemeWeno3 | kSchemeSignSplit))
+    rk_stage2d_kernel<STAGE, false, kSchemeWeno3 | kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
   else
     rk_stage2d_kernel<STAGE><<<grid, kS2T, 0, s>>>(a, sp);
   return cudaGetLastError();

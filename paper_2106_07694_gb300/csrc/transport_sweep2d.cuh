@@ -64,6 +64,45 @@ __device__ __forceinline__ float weno5_face_value(float a, float b, float c, flo
   return fmaf(__fdividef(num, den), 1.f / 6.f, c);
 }
 
+// The paper's third-order WENO face value (Supplement Eqs. S10, S11, S14-S16) on the
+// upwind-side values a, b, c = h_{i-1}, h_i, h_{i+1}: candidates (b + c)/2 and (3b - a)/2,
+// indicators (c - b)^2 and (b - a)^2, linear weights 2/3 and 1/3; one division.
+__device__ __forceinline__ float weno3_face_value(float a, float b, float c) {
+  const float eps = 1e-6f;
+  float a1 = fmaf(c - b, c - b, eps), a2 = fmaf(b - a, b - a, eps);
+  a1 *= a1;
+  a2 *= a2;
+  const float p1 = 2.f * a2;  // (2/3)/a1 : (1/3)/a2 over the common factor 1/(3 a1 a2)
+  return __fdividef(fmaf(p1, b + c, a1 * fmaf(3.f, b, -a)), 2.f * (p1 + a1));
+}
+
+// Face flux of a transport-scheme variant (SCHEME = kSchemeWeno3 | kSchemeSignSplit bits;
+// 0 is the Lax-Friedrichs WENO5 of face_flux_x) from the staged pairs of the six points
+// i-2 .. i+3 around the face i+1/2 (p[k], m[k] = point i-2+k).  Lax-Friedrichs schemes
+// stage p = h+/alpha, m = h-/alpha; the sign split stages p = w c/alpha, m = w/alpha and
+// reconstructs w c from the side the face velocity (w_i + w_{i+1})/2 comes from (ties
+// to the left).
+template <int SCHEME>
+__device__ __forceinline__ float face_flux_scheme(const float (&p)[6], const float (&m)[6], float alpha,
+                                                  float kappa, float cl, float cr) {
+  constexpr bool W3 = (SCHEME & kSchemeWeno3) != 0, SIGN = (SCHEME & kSchemeSignSplit) != 0;
+  float h;
+  if (SIGN) {
+    const bool left = m[2] + m[3] >= 0.f;
+    if (W3) {
+      h = weno3_face_value(left ? p[1] : p[4], left ? p[2] : p[3], left ? p[3] : p[2]);
+    } else {
+      h = weno5_face_value(left ? p[0] : p[5], left ? p[1] : p[4], left ? p[2] : p[3], left ? p[3] : p[2],
+                           left ? p[4] : p[1]);
+    }
+  } else if (W3) {
+    h = weno3_face_value(p[1], p[2], p[3]) + weno3_face_value(m[4], m[3], m[2]);
+  } else {
+    h = weno5_face_value(p[0], p[1], p[2], p[3], p[4]) + weno5_face_value(m[5], m[4], m[3], m[2], m[1]);
+  }
+  return fmaf(alpha, h, kappa * (cl - cr));
+}
+
 // Total face flux (unscaled): alpha (h+ + h-) + kappa (cl - cr), with h+ from the
 // left-biased values p0..p4 and h- from the right-biased values m0..m4 (already mirrored).
 __device__ __forceinline__ float face_flux_x(float p0, float p1, float p2, float p3, float p4, float m0,

@@ -45,8 +45,11 @@ struct Sweep3dParams {
   float ghost_shift; // 2 Vs / alpha
 };
 
-template <int STAGE, bool SUGAR>
+// SCHEME: transport-scheme variant bits (kSchemeWeno3, kSchemeSignSplit; 0 = Lax-Friedrichs
+// WENO5), see face_flux_scheme.
+template <int STAGE, bool SUGAR, int SCHEME>
 __device__ __forceinline__ void rk_sweep3d_body(const Args<float>& a, const Sweep3dParams& sp) {
+  constexpr bool SIGN = (SCHEME & kSchemeSignSplit) != 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sweep3dSmem& S = *reinterpret_cast<Sweep3dSmem*>(smem_raw);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kT3x + tx;
@@ -78,8 +81,8 @@ __device__ __forceinline__ void rk_sweep3d_body(const Args<float>& a, const Swee
   };
   auto col_put = [&](int l) {
     const float h = 0.5f * qc;
-    S.zp[l & (kT3r - 1)][ty][tx] = fmaf(qw, h, h);
-    S.zm[l & (kT3r - 1)][ty][tx] = fmaf(qw, h, -h);
+    S.zp[l & (kT3r - 1)][ty][tx] = SIGN ? qw * qc : fmaf(qw, h, h);
+    S.zm[l & (kT3r - 1)][ty][tx] = SIGN ? qw : fmaf(qw, h, -h);
     S.cz[l & (kT3r - 1)][ty][tx] = qc;
   };
   auto col_split = [&](int l) {
@@ -143,13 +146,13 @@ __device__ __forceinline__ void rk_sweep3d_body(const Args<float>& a, const Swee
         S.c[ry][rx] = c;
         if (sl_x[q]) {
           const float w = pu[q] * inv_alpha;
-          S.xp[ry - kT3h][rx] = fmaf(w, h, h);
-          S.xm[ry - kT3h][rx] = fmaf(w, h, -h);
+          S.xp[ry - kT3h][rx] = SIGN ? w * c : fmaf(w, h, h);
+          S.xm[ry - kT3h][rx] = SIGN ? w : fmaf(w, h, -h);
         }
         if (sl_y[q]) {
           const float w = pv[q] * inv_alpha;
-          S.yp[ry][rx - kT3h] = fmaf(w, h, h);
-          S.ym[ry][rx - kT3h] = fmaf(w, h, -h);
+          S.yp[ry][rx - kT3h] = SIGN ? w * c : fmaf(w, h, h);
+          S.ym[ry][rx - kT3h] = SIGN ? w : fmaf(w, h, -h);
         }
       }
     }
@@ -161,37 +164,72 @@ __device__ __forceinline__ void rk_sweep3d_body(const Args<float>& a, const Swee
     __syncthreads();
 
     // ---- faces: left x face and lower y face of this column, upper z face
-    if (!prime) {
-      const float* P = &S.xp[ty][tx];
-      const float* M = &S.xm[ty][tx];
-      S.fx[ty][tx] = face_flux_x(P[0], P[1], P[2], P[3], P[4], M[5], M[4], M[3], M[2], M[1], alpha, kappa,
-                                 S.c[ty + kT3h][tx + kT3h - 1], S.c[ty + kT3h][tx + kT3h]);
-      S.fy[ty][tx] = face_flux_x(S.yp[ty][tx], S.yp[ty + 1][tx], S.yp[ty + 2][tx], S.yp[ty + 3][tx],
-                                 S.yp[ty + 4][tx], S.ym[ty + 5][tx], S.ym[ty + 4][tx], S.ym[ty + 3][tx],
-                                 S.ym[ty + 2][tx], S.ym[ty + 1][tx], alpha, kappa, S.c[ty + kT3h - 1][tx + kT3h],
-                                 S.c[ty + kT3h][tx + kT3h]);
-      if (ty == 0 && tx < kT3y) {  // right edge x faces (column 32) of the tile rows
-        const float* Pe = &S.xp[tx][kT3x];
-        const float* Me = &S.xm[tx][kT3x];
-        S.fx[tx][kT3x] = face_flux_x(Pe[0], Pe[1], Pe[2], Pe[3], Pe[4], Me[5], Me[4], Me[3], Me[2], Me[1], alpha,
-                                     kappa, S.c[tx + kT3h][kT3x + kT3h - 1], S.c[tx + kT3h][kT3x + kT3h]);
+    float chere, fup = 0.f;
+    if constexpr (SCHEME == 0) {
+      if (!prime) {
+        const float* P = &S.xp[ty][tx];
+        const float* M = &S.xm[ty][tx];
+        S.fx[ty][tx] = face_flux_x(P[0], P[1], P[2], P[3], P[4], M[5], M[4], M[3], M[2], M[1], alpha, kappa,
+                                   S.c[ty + kT3h][tx + kT3h - 1], S.c[ty + kT3h][tx + kT3h]);
+        S.fy[ty][tx] = face_flux_x(S.yp[ty][tx], S.yp[ty + 1][tx], S.yp[ty + 2][tx], S.yp[ty + 3][tx],
+                                   S.yp[ty + 4][tx], S.ym[ty + 5][tx], S.ym[ty + 4][tx], S.ym[ty + 3][tx],
+                                   S.ym[ty + 2][tx], S.ym[ty + 1][tx], alpha, kappa, S.c[ty + kT3h - 1][tx + kT3h],
+                                   S.c[ty + kT3h][tx + kT3h]);
+        if (ty == 0 && tx < kT3y) {  // right edge x faces (column 32) of the tile rows
+          const float* Pe = &S.xp[tx][kT3x];
+          const float* Me = &S.xm[tx][kT3x];
+          S.fx[tx][kT3x] = face_flux_x(Pe[0], Pe[1], Pe[2], Pe[3], Pe[4], Me[5], Me[4], Me[3], Me[2], Me[1], alpha,
+                                       kappa, S.c[tx + kT3h][kT3x + kT3h - 1], S.c[tx + kT3h][kT3x + kT3h]);
+        }
+        if (ty == 1) {  // upper edge y faces (row 8) of the tile columns
+          S.fy[kT3y][tx] = face_flux_x(S.yp[kT3y][tx], S.yp[kT3y + 1][tx], S.yp[kT3y + 2][tx], S.yp[kT3y + 3][tx],
+                                       S.yp[kT3y + 4][tx], S.ym[kT3y + 5][tx], S.ym[kT3y + 4][tx],
+                                       S.ym[kT3y + 3][tx], S.ym[kT3y + 2][tx], S.ym[kT3y + 1][tx], alpha, kappa,
+                                       S.c[kT3y + kT3h - 1][tx + kT3h], S.c[kT3y + kT3h][tx + kT3h]);
+        }
       }
-      if (ty == 1) {  // upper edge y faces (row 8) of the tile columns
-        S.fy[kT3y][tx] = face_flux_x(S.yp[kT3y][tx], S.yp[kT3y + 1][tx], S.yp[kT3y + 2][tx], S.yp[kT3y + 3][tx],
-                                     S.yp[kT3y + 4][tx], S.ym[kT3y + 5][tx], S.ym[kT3y + 4][tx],
-                                     S.ym[kT3y + 3][tx], S.ym[kT3y + 2][tx], S.ym[kT3y + 1][tx], alpha, kappa,
-                                     S.c[kT3y + kT3h - 1][tx + kT3h], S.c[kT3y + kT3h][tx + kT3h]);
+      chere = S.cz[k & (kT3r - 1)][ty][tx];
+      if (k != nz - 1) {
+        fup = face_flux_x(S.zp[(k - 2) & (kT3r - 1)][ty][tx], S.zp[(k - 1) & (kT3r - 1)][ty][tx],
+                          S.zp[k & (kT3r - 1)][ty][tx], S.zp[(k + 1) & (kT3r - 1)][ty][tx],
+                          S.zp[(k + 2) & (kT3r - 1)][ty][tx], S.zm[(k + 3) & (kT3r - 1)][ty][tx],
+                          S.zm[(k + 2) & (kT3r - 1)][ty][tx], S.zm[(k + 1) & (kT3r - 1)][ty][tx],
+                          S.zm[k & (kT3r - 1)][ty][tx], S.zm[(k - 1) & (kT3r - 1)][ty][tx], alpha, kappa, chere,
+                          S.cz[(k + 1) & (kT3r - 1)][ty][tx]);
       }
-    }
-    const float chere = S.cz[k & (kT3r - 1)][ty][tx];
-    float fup = 0.f;
-    if (k != nz - 1) {
-      fup = face_flux_x(S.zp[(k - 2) & (kT3r - 1)][ty][tx], S.zp[(k - 1) & (kT3r - 1)][ty][tx],
-                        S.zp[k & (kT3r - 1)][ty][tx], S.zp[(k + 1) & (kT3r - 1)][ty][tx],
-                        S.zp[(k + 2) & (kT3r - 1)][ty][tx], S.zm[(k + 3) & (kT3r - 1)][ty][tx],
-                        S.zm[(k + 2) & (kT3r - 1)][ty][tx], S.zm[(k + 1) & (kT3r - 1)][ty][tx],
-                        S.zm[k & (kT3r - 1)][ty][tx], S.zm[(k - 1) & (kT3r - 1)][ty][tx], alpha, kappa, chere,
-                        S.cz[(k + 1) & (kT3r - 1)][ty][tx]);
+    } else {
+      // the six staged pairs of a face at stride st from P, M (points i-2 .. i+3)
+      auto face6 = [&](const float* P, const float* M, int st, float cl, float cr) {
+        float p[6], m[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          p[q] = P[q * st];
+          m[q] = M[q * st];
+        }
+        return face_flux_scheme<SCHEME>(p, m, alpha, kappa, cl, cr);
+      };
+      if (!prime) {
+        S.fx[ty][tx] =
+            face6(&S.xp[ty][tx], &S.xm[ty][tx], 1, S.c[ty + kT3h][tx + kT3h - 1], S.c[ty + kT3h][tx + kT3h]);
+        S.fy[ty][tx] = face6(&S.yp[ty][tx], &S.ym[ty][tx], kT3x, S.c[ty + kT3h - 1][tx + kT3h],
+                             S.c[ty + kT3h][tx + kT3h]);
+        if (ty == 0 && tx < kT3y)  // right edge x faces (column 32) of the tile rows
+          S.fx[tx][kT3x] = face6(&S.xp[tx][kT3x], &S.xm[tx][kT3x], 1, S.c[tx + kT3h][kT3x + kT3h - 1],
+                                 S.c[tx + kT3h][kT3x + kT3h]);
+        if (ty == 1)  // upper edge y faces (row 8) of the tile columns
+          S.fy[kT3y][tx] = face6(&S.yp[kT3y][tx], &S.ym[kT3y][tx], kT3x, S.c[kT3y + kT3h - 1][tx + kT3h],
+                                 S.c[kT3y + kT3h][tx + kT3h]);
+      }
+      chere = S.cz[k & (kT3r - 1)][ty][tx];
+      if (k != nz - 1) {
+        float p[6], m[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          p[q] = S.zp[(k - 2 + q) & (kT3r - 1)][ty][tx];
+          m[q] = S.zm[(k - 2 + q) & (kT3r - 1)][ty][tx];
+        }
+        fup = face_flux_scheme<SCHEME>(p, m, alpha, kappa, chere, S.cz[(k + 1) & (kT3r - 1)][ty][tx]);
+      }
     }
     __syncthreads();
 
@@ -223,25 +261,38 @@ __device__ __forceinline__ void rk_sweep3d_body(const Args<float>& a, const Swee
 // capped at 64 registers (four resident 256-thread CTAs per SM) for the instantiations the
 // compiler would otherwise give more (stage 3: 72; stage 1 with sugar).  An explicit
 // minimum of one block is not the same as none: it lets stages 1 and 2 grow to 72.
-template <int STAGE, bool SUGAR = false>
+template <int STAGE, bool SUGAR = false, int SCHEME = 0>
 __global__ void __launch_bounds__(kT3x * kT3y) rk_sweep3d_kernel(Args<float> a, Sweep3dParams sp) {
-  rk_sweep3d_body<STAGE, SUGAR>(a, sp);
+  rk_sweep3d_body<STAGE, SUGAR, SCHEME>(a, sp);
 }
 
-template <int STAGE, bool SUGAR = false>
+template <int STAGE, bool SUGAR = false, int SCHEME = 0>
 __global__ void __launch_bounds__(kT3x * kT3y, 4) rk_sweep3d_capped_kernel(Args<float> a, Sweep3dParams sp) {
-  rk_sweep3d_body<STAGE, SUGAR>(a, sp);
+  rk_sweep3d_body<STAGE, SUGAR, SCHEME>(a, sp);
 }
 
 template <int STAGE, bool SUGAR>
 constexpr bool sweep3d_capped() { return (STAGE == 3 && !SUGAR) || (STAGE == 1 && SUGAR); }
 
-template <int STAGE, bool SUGAR>
+template <int STAGE, bool SUGAR, int SCHEME = 0>
 inline void (*sweep3d_entry())(Args<float>, Sweep3dParams) {
   if constexpr (sweep3d_capped<STAGE, SUGAR>())
-    return rk_sweep3d_capped_kernel<STAGE, SUGAR>;
+    return rk_sweep3d_capped_kernel<STAGE, SUGAR, SCHEME>;
   else
-    return rk_sweep3d_kernel<STAGE, SUGAR>;
+    return rk_sweep3d_kernel<STAGE, SUGAR, SCHEME>;
+}
+
+// The entry point of a stage for the handle's arguments (the scheme variants have no
+// sugar instantiation: those handles take the generic path).
+template <int STAGE>
+inline void (*sweep3d_entry_for(const Args<float>& a))(Args<float>, Sweep3dParams) {
+  if (a.S) return sweep3d_entry<STAGE, true>();
+  switch (a.scheme) {
+    case kSchemeWeno3: return sweep3d_entry<STAGE, false, kSchemeWeno3>();
+    case kSchemeSignSplit: return sweep3d_entry<STAGE, false, kSchemeSignSplit>();
+    case kSchemeWeno3 | kSchemeSignSplit: return sweep3d_entry<STAGE, false, kSchemeWeno3 | kSchemeSignSplit>();
+    default: return sweep3d_entry<STAGE, false>();
+  }
 }
 
 inline size_t sweep3d_smem() { return sizeof(Sweep3dSmem); }
@@ -251,12 +302,18 @@ inline bool sweep3d_supported(int nz, bool walls) { return walls && nz >= 4; }
 inline cudaError_t sweep3d_prepare() {
   const int b = (int)sizeof(Sweep3dSmem);
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(sweep3d_entry<1, false>(), at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<2, false>(), at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<3, false>(), at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<1, true>(), at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<2, true>(), at, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep3d_entry<3, true>(), at, b);
+  void (*const entries[])(Args<float>, Sweep3dParams) = {
+      sweep3d_entry<1, false>(), sweep3d_entry<2, false>(), sweep3d_entry<3, false>(),
+      sweep3d_entry<1, true>(), sweep3d_entry<2, true>(), sweep3d_entry<3, true>(),
+      sweep3d_entry<1, false, kSchemeWeno3>(), sweep3d_entry<2, false, kSchemeWeno3>(),
+      sweep3d_entry<3, false, kSchemeWeno3>(), sweep3d_entry<1, false, kSchemeSignSplit>(),
+      sweep3d_entry<2, false, kSchemeSignSplit>(), sweep3d_entry<3, false, kSchemeSignSplit>(),
+      sweep3d_entry<1, false, kSchemeWeno3 | kSchemeSignSplit>(),
+      sweep3d_entry<2, false, kSchemeWeno3 | kSchemeSignSplit>(),
+      sweep3d_entry<3, false, kSchemeWeno3 | kSchemeSignSplit>()};
+  cudaError_t e = cudaSuccess;
+  for (auto f : entries)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, at, b);
   return e;
 }
 
@@ -278,10 +335,7 @@ inline cudaError_t launch_sweep3d(const Args<float>& a, const float* cin, float*
   sp.H = H;
   sp.ghost_shift = 2.f * a.vs * a.inv_alpha;
   const dim3 grid((a.nx + kT3x - 1) / kT3x, (a.ny + kT3y - 1) / kT3y, (a.nz + H - 1) / H);
-  if (a.S)
-    sweep3d_entry<STAGE, true>()<<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
-  else
-    sweep3d_entry<STAGE, false>()<<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
+  sweep3d_entry_for<STAGE>(a)<<<grid, dim3(kT3x, kT3y), sizeof(Sweep3dSmem), s>>>(a, sp);
   return cudaGetLastError();
 }
 

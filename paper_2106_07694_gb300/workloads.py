@@ -82,6 +82,22 @@ class Workload:
         """Keyword parameters of the sugar scalar ({} when the workload has none)."""
         return dict(self.extra.get("sugar", {}))
 
+    @property
+    def scheme(self) -> dict:
+        """Keyword parameters of a transport-scheme variant ({} for flux-split WENO5)."""
+        return dict(self.extra.get("scheme", {}))
+
+    @property
+    def class_vs(self) -> tuple:
+        """Settling velocities of the particle classes (() for one class)."""
+        return tuple(self.extra.get("class_vs", ()))
+
+    def initial_classes(self) -> list:
+        """Initial class fields: the interface field shared equally between the classes."""
+        c0 = self.initial_c()
+        k = len(self.class_vs)
+        return [c0 / k for _ in range(k)]
+
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
 
@@ -109,6 +125,14 @@ SUGAR_2D = Workload("d2q9_2048x4096_f32_sugar", (2048, 4096), "f32", 20000, grav
                     extra=dict(interface_frac=0.5,
                                sugar=dict(sugar=True, sugar_contrast=8.4e-3, sugar_diffusivity=1.7e-5,
                                           phi0=1.19e-3, vs_sugar=5.53e-3)))
+
+# Variants of the 2048 x 4096 case: the paper's third-order WENO (two stencils, weights 2/3
+# and 1/3), the sign-upwind choice of the WENO5 stencil in place of the Lax-Friedrichs split,
+# and three particle classes (settling velocities spanning the sweep grid's range, each
+# class a third of the interface field, phi_tot = sum of the classes).
+WENO3_2D = MAIN_2D.with_(name="d2q9_2048x4096_f32_weno3", extra=dict(scheme=dict(weno3=True)))
+SIGN_SPLIT_2D = MAIN_2D.with_(name="d2q9_2048x4096_f32_signsplit", extra=dict(scheme=dict(sign_split=True)))
+CLASSES_2D = MAIN_2D.with_(name="d2q9_2048x4096_f32_3classes", extra=dict(class_vs=(5e-4, 1e-3, 2e-3)))
 
 # Sweep grid of the 2048 x 4096 case: buoyancy amplitude x settling velocity.
 MAIN_2D_SWEEP = [(a, vs) for a in (1e-5, 2e-5, 5e-5) for vs in (5e-4, 1e-3, 2e-3)]

@@ -1,7 +1,8 @@
 """Parity of the flux variants (the paper's third-order WENO, Supplement Eqs. S10-S20, and
 the split by the sign of the face velocity) with the FP64 oracle, through the C ABI:
-FP64 to 1e-12, FP32 to 1e-5 before the flow saturates, 2D walls with a ragged width,
-D3Q19, and with the sugar scalar."""
+FP64 to 1e-12, FP32 to 1e-5 before the flow saturates, 2D walls with a ragged width (the
+FP32 row-sweep stage kernels, several segment heights), D3Q19 (FP64 generic kernels; FP32
+tiled z-sweep), and with the sugar scalar (the generic stage kernels)."""
 import numpy as np
 import pytest
 
@@ -56,11 +57,56 @@ def test_variant_2d_matches_oracle(variant, fp64, tol):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+def test_variant_2d_fp32_row_segments(variant):
+    """The FP32 row-sweep stage kernels with a variant: three strips (the last 4 columns
+    wide), 16-row and ragged 5-row segments; both match the oracle to 1e-5 and each other
+    bit for bit (every face is computed once, whatever the segmentation)."""
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    shape = (260, 96)
+    c0 = workloads.interface_field(shape, interface_frac=0.6, amplitude=0.02, seed=11)
+    c0 = c0.astype(np.float32).astype(np.float64)
+    o = oracle.OracleSim(shape, **STRONG, **variant)
+    o.init(c0)
+    o.step(30)
+    out = []
+    for rows in (16, 5):
+        g = lw.Simulation(shape, fp64=False, **STRONG, **variant)
+        lw.lbm_wenoc_set_segment_rows(g.handle, rows)
+        g.init(c0)
+        g.step(30)
+        _check(g, o, 1e-5, 1e-12)
+        out.append(to_np(g.fields()[2]))
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_variant_d3q19_matches_oracle(variant):
     shape = (16, 12, 24)
     c0 = workloads.interface_field(shape, interface_frac=0.6, amplitude=0.02, seed=8)
     g, o = _run(shape, c0, 12, True, **STRONG, **variant)
     _check(g, o, 1e-12, 1e-15)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variant_d3q19_fp32_sweep(variant):
+    """The FP32 tiled z-sweep stage kernels with a variant: ragged tiles in x and y, 24- and
+    7-level segments; both match the oracle to 1e-5 and each other bit for bit."""
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    shape = (36, 20, 40)
+    c0 = workloads.interface_field(shape, interface_frac=0.6, amplitude=0.02, seed=12)
+    c0 = c0.astype(np.float32).astype(np.float64)
+    o = oracle.OracleSim(shape, **STRONG, **variant)
+    o.init(c0)
+    o.step(12)
+    out = []
+    for rows in (24, 7):
+        g = lw.Simulation(shape, fp64=False, **STRONG, **variant)
+        lw.lbm_wenoc_set_segment_rows(g.handle, rows)
+        g.init(c0)
+        g.step(12)
+        _check(g, o, 1e-5, 1e-12)
+        out.append(to_np(g.fields()[2]))
+    assert np.array_equal(out[0], out[1])
 
 
 def test_variant_with_sugar_matches_oracle():
