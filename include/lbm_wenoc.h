@@ -123,6 +123,16 @@ int lbm_wenoc_deposited_mass(lbm_wenoc* h, double* out);
 /* Synchronise and return sum of c over the domain (FP64, fixed summation order). */
 int lbm_wenoc_total_mass(lbm_wenoc* h, double* out);
 
+/* Particle mass below a horizontal plane (Sec. 4.2.3, Eq. flux): the sum of c over the
+ * vertical levels 0 .. level-1 (FP64, fixed summation order; the sum of the classes with
+ * several) plus the deposited mass, which has crossed every plane.  The mass flux through
+ * the plane between two calls Delta t apart is J = (m(t) - m(t - Delta t)) / (A Delta t),
+ * A = nx (2D) or nx ny (3D), in lattice units (m_i = c_i: unit cell volume and particle
+ * density).  0 <= level <= ny (2D) or nz (3D), else LW_EINVAL; level = 0 gives the
+ * deposit, the top level total_mass + deposit.  Synchronises the stream; LW_EUNSTABLE as
+ * lbm_wenoc_deposited_mass (the value is still written). */
+int lbm_wenoc_mass_below(lbm_wenoc* h, int32_t level, double* out);
+
 /* Write the macroscopic state of the current step: rho[n], u[dim*n] (half-force
  * corrected velocity (sum f c + F/2)/rho with the current c), c[n].  Any pointer may
  * be NULL; each may be host or device memory.  Synchronises. */

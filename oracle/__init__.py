@@ -69,6 +69,8 @@ def lib():
         L.orc_deposit.restype = ctypes.c_double
         L.orc_total_mass.argtypes = [ctypes.c_void_p]
         L.orc_total_mass.restype = ctypes.c_double
+        L.orc_mass_below.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_mass_below.restype = ctypes.c_double
         L.orc_alpha.argtypes = [ctypes.c_void_p]
         L.orc_alpha.restype = ctypes.c_double
         L.orc_steps.argtypes = [ctypes.c_void_p]
@@ -250,6 +252,11 @@ class OracleSim:
     @property
     def total_mass(self):
         return lib().orc_total_mass(self._h)
+
+    def mass_below(self, level):
+        """Mass below the plane under vertical level `level`, deposit included (Sec. 4.2.3,
+        Eq. flux)."""
+        return lib().orc_mass_below(self._h, int(level))
 
     @property
     def steps(self):

@@ -719,6 +719,22 @@ double orc_total_mass(const orc_sim *s) {
   return acc;
 }
 
+/* Particle mass below the horizontal plane under vertical level `level` (Sec. 4.2.3,
+ * Eq. flux: the mass in the volume below the plane, m_i = c_i in lattice units), plus
+ * the deposited mass, which lies below every plane: the cells with vertical index
+ * v < level, summed serially in index order.  Returns NaN for a level outside 0..N. */
+double orc_mass_below(const orc_sim *s, int level) {
+  const int vax = s->p.dim - 1;
+  const int nv = s->n[vax];
+  if (level < 0 || level > nv) return NAN;
+  double acc = 0.0;
+  for (size_t k = 0; k < s->nn; ++k) {
+    const int v = (int)(k / ((size_t)s->nn / (size_t)nv));  /* vertical index: the slowest axis */
+    if (v < level) acc += s->ncls > 1 ? s->ctot[k] : s->c[k];
+  }
+  return acc + s->deposit;
+}
+
 /* L(c) for a given c and transport velocity u (dim*nn), using the walls and
  * parameters of the simulation; used to pin the spatial operator alone. */
 void orc_transport_rate(orc_sim *s, const double *c, const double *u, double *L) {

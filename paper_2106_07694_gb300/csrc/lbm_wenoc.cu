@@ -663,19 +663,22 @@ int lbm_wenoc_deposited_mass(lbm_wenoc* h, double* out) {
   return rc;
 }
 
-int lbm_wenoc_total_mass(lbm_wenoc* h, double* out) {
-  if (!h || !out) return LW_EINVAL;
-  if (!h->initialised) return LW_ESTATE;
-  const int blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (h->n + 8191) / 8192);
+// Sum of c (or of the classes) over the first `count` nodes, FP64 in a fixed order, into *out.
+static int sum_c(lbm_wenoc* h, long long count, double* out) {
+  if (count <= 0) {
+    *out = 0.0;
+    return LW_OK;
+  }
+  const int blocks = (int)std::min<long long>(lw::kMaxReduceBlocks, (count + 8191) / 8192);
   const bool classes = h->ncls > 1;  // the sum of the classes
   if (h->fp64) {
     Args<double> a = make_args<double>(h);
     const double* src = classes ? reinterpret_cast<const double*>(h->ws + h->L.ctot) : a.c;
-    lw::sum_kernel<double><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, src, h->n);
+    lw::sum_kernel<double><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, src, count);
   } else {
     Args<float> a = make_args<float>(h);
     const float* src = classes ? reinterpret_cast<const float*>(h->ws + h->L.ctot) : a.c;
-    lw::sum_kernel<float><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, src, h->n);
+    lw::sum_kernel<float><<<blocks, lw::kReduceThreads, 0, h->stream>>>(a, src, count);
   }
   if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
@@ -683,6 +686,27 @@ int lbm_wenoc_total_mass(lbm_wenoc* h, double* out) {
       cudaSuccess)
     return LW_ECUDA;
   return LW_OK;
+}
+
+int lbm_wenoc_total_mass(lbm_wenoc* h, double* out) {
+  if (!h || !out) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  return sum_c(h, h->n, out);
+}
+
+int lbm_wenoc_mass_below(lbm_wenoc* h, int32_t level, double* out) {
+  if (!h || !out) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const int nv = h->p.dim == 3 ? h->p.nz : h->p.ny;
+  if (level < 0 || level > nv) return LW_EINVAL;
+  // the vertical axis is the slowest: the levels below the plane are the first nodes
+  double below = 0.0, dep = 0.0;
+  int rc = sum_c(h, (long long)level * (h->n / nv), &below);
+  if (rc != LW_OK) return rc;
+  rc = lbm_wenoc_deposited_mass(h, &dep);
+  if (rc != LW_OK && rc != LW_EUNSTABLE) return rc;
+  *out = below + dep;
+  return rc;
 }
 
 int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {

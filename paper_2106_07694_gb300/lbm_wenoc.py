@@ -35,7 +35,8 @@ _ERRORS = {LW_EINVAL: "LW_EINVAL", LW_ENOMEM: "LW_ENOMEM", LW_ECUDA: "LW_ECUDA",
 
 EXPORTED = [
     "lbm_wenoc_workspace_bytes", "lbm_wenoc_create", "lbm_wenoc_init", "lbm_wenoc_step",
-    "lbm_wenoc_deposited_mass", "lbm_wenoc_total_mass", "lbm_wenoc_fields", "lbm_wenoc_status",
+    "lbm_wenoc_deposited_mass", "lbm_wenoc_total_mass", "lbm_wenoc_mass_below", "lbm_wenoc_fields",
+    "lbm_wenoc_status",
     "lbm_wenoc_steps", "lbm_wenoc_profile_enable", "lbm_wenoc_profile_read",
     "lbm_wenoc_launch_count", "lbm_wenoc_set_segment_rows", "lbm_wenoc_total_mass_noalloc",
     "lbm_wenoc_destroy", "lbm_wenoc_batch_workspace_bytes", "lbm_wenoc_batch_create",
@@ -104,6 +105,7 @@ def load():
     L.lbm_wenoc_step.argtypes = [vp, i64]
     L.lbm_wenoc_deposited_mass.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.lbm_wenoc_total_mass.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.lbm_wenoc_mass_below.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     L.lbm_wenoc_fields.argtypes = [vp, vp, vp, vp]
     L.lbm_wenoc_status.argtypes = [vp]
     L.lbm_wenoc_steps.argtypes = [vp]
@@ -192,6 +194,12 @@ def lbm_wenoc_deposited_mass(h):
 def lbm_wenoc_total_mass(h):
     out = ctypes.c_double()
     _check("lbm_wenoc_total_mass", load().lbm_wenoc_total_mass(h, ctypes.byref(out)))
+    return out.value
+
+
+def lbm_wenoc_mass_below(h, level):
+    out = ctypes.c_double()
+    _check("lbm_wenoc_mass_below", load().lbm_wenoc_mass_below(h, int(level), ctypes.byref(out)))
     return out.value
 
 
@@ -376,6 +384,11 @@ class Simulation:
     @property
     def total_mass(self):
         return lbm_wenoc_total_mass(self.handle)
+
+    def mass_below(self, level):
+        """Particle mass below the horizontal plane under vertical level `level`, deposit
+        included (Sec. 4.2.3, Eq. flux): J = (m(t) - m(t - dt)) / (A dt)."""
+        return lbm_wenoc_mass_below(self.handle, level)
 
     @property
     def steps(self):
