@@ -37,44 +37,51 @@ struct AdjFields {
   double* vs_part;  // per-CTA partial sums of dJ/dVs, accumulated over stages and steps
 };
 
+// Fused multiply-add in the working precision.
+__device__ __forceinline__ float fmaf_t(float x, float y, float z) { return fmaf(x, y, z); }
+__device__ __forceinline__ double fmaf_t(double x, double y, double z) { return fma(x, y, z); }
+
 // Reciprocal for the derivative weights: MUFU reciprocal (2 ulp) in FP32, exact in FP64.
 __device__ __forceinline__ float adj_rcp(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double adj_rcp(double x) { return 1.0 / x; }
 
 // WENO5-JS face value of the scaled values v[0..4] (upwind side first) and its partial
 // derivatives dv[0..4]: sum_k w_k dq_k/dv_j + sum_m (q_m - val) w_m (-2/(eps+beta_m)) dbeta_m/dv_j.
+// Written on the first differences d1..d4 (candidates relative to the centre value c:
+// 6 (q_m - c) = 5 d2 - 2 d1, d2 + 2 d3, 4 d3 - d4; s_m, t_m as in the indicators below).
+// The weights depend only on ratios of (eps + beta_m)^2, so beta_m and eps are scaled by
+// 12/13: beta'_m = s_m^2 + k t_m^2 with k = 3/13, and d beta'_m/dv = 2 (s_m ds_m + k t_m dt_m),
+// the factor 2 folded into the weight-sensitivity factors r_m.
 template <typename T>
 __device__ __forceinline__ T weno5_value_grad(const T (&v)[5], T (&dv)[5]) {
   const T a = v[0], b = v[1], c = v[2], d = v[3], e = v[4];
-  const T eps = T(1e-6), sixth = T(1.0 / 6.0);
-  const T q0 = (T(2) * a - T(7) * b + T(11) * c) * sixth;
-  const T q1 = (-b + T(5) * c + T(2) * d) * sixth;
-  const T q2 = (T(2) * c + T(5) * d - e) * sixth;
-  const T s0 = a - T(2) * b + c, s1 = b - T(2) * c + d, s2 = c - T(2) * d + e;
-  const T t0 = a - T(4) * b + T(3) * c, t1 = b - d, t2 = T(3) * c - T(4) * d + e;
-  // reciprocals of eps + beta_m and of the weight sum: four in all
-  const T i0 = adj_rcp(eps + T(13.0 / 12.0) * s0 * s0 + T(0.25) * t0 * t0);
-  const T i1 = adj_rcp(eps + T(13.0 / 12.0) * s1 * s1 + T(0.25) * t1 * t1);
-  const T i2 = adj_rcp(eps + T(13.0 / 12.0) * s2 * s2 + T(0.25) * t2 * t2);
+  const T d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
+  const T dq0 = fmaf_t(T(5.0 / 6.0), d2, T(-1.0 / 3.0) * d1);
+  const T dq1 = fmaf_t(T(1.0 / 3.0), d3, T(1.0 / 6.0) * d2);
+  const T dq2 = fmaf_t(T(2.0 / 3.0), d3, T(-1.0 / 6.0) * d4);
+  const T s0 = d2 - d1, s1 = d3 - d2, s2 = d4 - d3;            // a - 2b + c, b - 2c + d, c - 2d + e
+  const T t0 = fmaf_t(T(3), d2, -d1), t1 = d2 + d3, t2 = fmaf_t(T(-3), d3, d4);  // a - 4b + 3c, d - b, 3c - 4d + e
+  const T k = T(3.0 / 13.0), eps = T(1e-6 * 12.0 / 13.0);
+  const T kt0 = k * t0, kt1 = k * t1, kt2 = k * t2;
+  // reciprocals of eps' + beta'_m and of the weight sum: four in all
+  const T i0 = adj_rcp(fmaf_t(s0, s0, fmaf_t(kt0, t0, eps)));
+  const T i1 = adj_rcp(fmaf_t(s1, s1, fmaf_t(kt1, t1, eps)));
+  const T i2 = adj_rcp(fmaf_t(s2, s2, fmaf_t(kt2, t2, eps)));
   const T a0 = T(0.1) * i0 * i0, a1 = T(0.6) * i1 * i1, a2 = T(0.3) * i2 * i2;
   const T inv = adj_rcp(a0 + a1 + a2);
   const T w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
-  const T val = w0 * q0 + w1 * q1 + w2 * q2;
-  // weight-sensitivity factors r_m = (q_m - val) w_m (-2 / (eps + beta_m))
-  const T r0 = T(-2) * (q0 - val) * w0 * i0;
-  const T r1 = T(-2) * (q1 - val) * w1 * i1;
-  const T r2 = T(-2) * (q2 - val) * w2 * i2;
-  // dbeta_m/dv = 13/6 s_m ds_m + 1/2 t_m dt_m
-  const T u0 = T(13.0 / 6.0) * s0, p0 = T(0.5) * t0;
-  const T u1 = T(13.0 / 6.0) * s1, p1 = T(0.5) * t1;
-  const T u2 = T(13.0 / 6.0) * s2, p2 = T(0.5) * t2;
-  dv[0] = w0 * T(1.0 / 3.0) + r0 * (u0 + p0);
-  dv[1] = w0 * T(-7.0 / 6.0) + w1 * T(-1.0 / 6.0) + r0 * (T(-2) * u0 - T(4) * p0) + r1 * (u1 + p1);
-  dv[2] = w0 * T(11.0 / 6.0) + w1 * T(5.0 / 6.0) + w2 * T(1.0 / 3.0) + r0 * (u0 + T(3) * p0) +
-          r1 * (T(-2) * u1) + r2 * (u2 + T(3) * p2);
-  dv[3] = w1 * T(1.0 / 3.0) + w2 * T(5.0 / 6.0) + r1 * (u1 - p1) + r2 * (T(-2) * u2 - T(4) * p2);
-  dv[4] = w2 * T(-1.0 / 6.0) + r2 * (u2 + p2);
-  return val;
+  const T dval = fmaf_t(w2, dq2, fmaf_t(w1, dq1, w0 * dq0));  // val - c
+  // weight-sensitivity factors 2 r_m = -4 (q_m - val) w_m / (eps' + beta'_m)
+  const T r0 = T(-4) * (dq0 - dval) * (w0 * i0);
+  const T r1 = T(-4) * (dq1 - dval) * (w1 * i1);
+  const T r2 = T(-4) * (dq2 - dval) * (w2 * i2);
+  dv[0] = w0 * T(1.0 / 3.0) + r0 * (s0 + kt0);
+  dv[1] = w0 * T(-7.0 / 6.0) + w1 * T(-1.0 / 6.0) + r0 * (T(-2) * s0 - T(4) * kt0) + r1 * (s1 - kt1);
+  dv[2] = w0 * T(11.0 / 6.0) + w1 * T(5.0 / 6.0) + w2 * T(1.0 / 3.0) + r0 * (s0 + T(3) * kt0) +
+          r1 * (T(-2) * s1) + r2 * (s2 + T(3) * kt2);
+  dv[3] = w1 * T(1.0 / 3.0) + w2 * T(5.0 / 6.0) + r1 * (s1 + kt1) + r2 * (T(-2) * s2 - T(4) * kt2);
+  dv[4] = w2 * T(-1.0 / 6.0) + r2 * (s2 + kt2);
+  return c + dval;
 }
 
 // Adjoint of one face flux F = alpha (v+ + v-) + kappa (c_0 - c_1) (face between stencil
@@ -375,24 +382,22 @@ __global__ void __launch_bounds__(128) adj_gather_fluid_kernel(Args<T> a, AdjFie
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= a.nx) return;
-  const long long n = a.n;
-  const long long node = (long long)y * a.nx + x;
+  const unsigned n = (unsigned)a.n;  // 24 n < 2^31 (checked by the host)
+  const D2Q9Node nd = d2q9_node(a, x, y);
+  const unsigned node = nd.node;
   T lc, gx, gy;
   gather_node<T, 1>(a, f, fr, x, y, lc, gx, gy);
   const T Fx = a.bf[0], Fy = a.bf[1] - a.A * a.c[node];
   const T rho = rho_rec[node];
   const T ux = a.u[node], uy = a.u[n + node];
   const T uu = ux * ux + uy * uy;
-  // adjoint of the post-collision populations: reverse streaming with bounce-back
+  // adjoint of the post-collision populations: reverse streaming with bounce-back (the
+  // population pushed to node + c_i, or bounced back into opp(i) here at a wall)
   T mu[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    long long dst;
-    if (neighbour<D2Q9>(i, +1, x, y, 0, a.nx, a.ny, 1, a.walls != 0, dst))
-      mu[i] = lam_next[i * n + dst];
-    else
-      mu[i] = lam_next[D2Q9::opp(i) * n + node];
-  }
+  for (int i = 0; i < 9; ++i)
+    mu[i] = nd.behind_wall(i, +1) ? lam_next[D2Q9::opp(i) * n + node]
+                                  : lam_next[i * n + (unsigned)((int)node + nd.off(i, +1))];
   T lam_drho = T(0), lux = f.lam_u[node] + gx, luy = f.lam_u[n + node] + gy, lFy = T(0);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -408,9 +413,10 @@ __global__ void __launch_bounds__(128) adj_gather_fluid_kernel(Args<T> a, AdjFie
     lFy += ks * (T(3) * cy - T(3) * uy + T(9) * cu * cy);
   }
   // u = (j + F/2)/rho
-  const T ljx = lux / rho, ljy = luy / rho;
-  lFy += luy / (T(2) * rho);
-  lam_drho -= (lux * ux + luy * uy) / rho;
+  const T irho = T(1) / rho;
+  const T ljx = lux * irho, ljy = luy * irho;
+  lFy += T(0.5) * ljy;
+  lam_drho -= (lux * ux + luy * uy) * irho;
   const T keep = T(1) - a.omega;
 #pragma unroll
   for (int i = 0; i < 9; ++i)

@@ -1270,25 +1270,36 @@ int adjoint_step(lbm_wenoc* h, const StepRecord<T>& R, const lw::AdjFields<T>& f
   return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
-// A second stream and its events for the recompute that overlaps the reverse sweep.
+// The streams of the reverse sweep: `rev`, at the device's greatest stream priority, runs
+// the reverse steps (the critical path); `s`, at the default (least) priority, the
+// recompute of the next segment, which then only takes the SMs the reverse kernels leave.
 struct RecomputeStream {
   cudaStream_t s = nullptr;
+  cudaStream_t rev = nullptr;
   cudaEvent_t rec_done[2] = {nullptr, nullptr};  // records of set i written
   cudaEvent_t rev_done[2] = {nullptr, nullptr};  // records of set i no longer read
+  cudaEvent_t join[2] = {nullptr, nullptr};      // caller's stream -> rev, rev -> caller's stream
   bool ok = false;
   RecomputeStream() {
-    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    int least = 0, greatest = 0;
+    ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&rev, cudaStreamNonBlocking, greatest) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i)
       ok = cudaEventCreateWithFlags(&rec_done[i], cudaEventDisableTiming) == cudaSuccess &&
-           cudaEventCreateWithFlags(&rev_done[i], cudaEventDisableTiming) == cudaSuccess;
+           cudaEventCreateWithFlags(&rev_done[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
   }
   ~RecomputeStream() {
     if (s) cudaStreamSynchronize(s);
+    if (rev) cudaStreamSynchronize(rev);
     for (int i = 0; i < 2; ++i) {
       if (rec_done[i]) cudaEventDestroy(rec_done[i]);
       if (rev_done[i]) cudaEventDestroy(rev_done[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
     }
     if (s) cudaStreamDestroy(s);
+    if (rev) cudaStreamDestroy(rev);
   }
 };
 
@@ -1348,7 +1359,10 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   // while the reverse of sg runs on the handle's stream, the recompute of sg - 1 runs on a
   // second stream into the other set, after the reverse of sg + 1 has released it.
   RecomputeStream rs;
-  if (G.nseg > 1 && !rs.ok) return LW_ECUDA;
+  if (!rs.ok) return LW_ECUDA;
+  // the reverse steps run on rs.rev after everything queued so far on the caller's stream
+  if (cudaEventRecord(rs.join[0], s) != cudaSuccess || cudaStreamWaitEvent(rs.rev, rs.join[0], 0) != cudaSuccess)
+    return LW_ECUDA;
   auto recompute = [&](int64_t sg) -> int {
     h->stream = rs.s;
     int r = LW_OK;
@@ -1361,20 +1375,32 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
       r = record_segment(sg);
     }
     if (r == LW_OK && cudaEventRecord(rs.rec_done[set_of(sg)], rs.s) != cudaSuccess) r = LW_ECUDA;
-    h->stream = s;
+    h->stream = rs.rev;
     return r;
   };
   int cur = 0;
+  h->stream = rs.rev;
   for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
-    if (sg >= 1 && (rc = recompute(sg - 1)) != LW_OK) return rc;
-    if (sg != G.nseg - 1 && cudaStreamWaitEvent(s, rs.rec_done[set_of(sg)], 0) != cudaSuccess) return LW_ECUDA;
-    for (int64_t k = seg_len(sg) - 1; k >= 0; --k) {
-      if ((rc = adjoint_step<T>(h, step_record<T>(aw, G, set_of(sg), k), f, fr, lg[cur], lg[cur ^ 1])) != LW_OK)
-        return rc;
+    if (sg >= 1 && (rc = recompute(sg - 1)) != LW_OK) break;
+    if (sg != G.nseg - 1 && cudaStreamWaitEvent(rs.rev, rs.rec_done[set_of(sg)], 0) != cudaSuccess) {
+      rc = LW_ECUDA;
+      break;
+    }
+    for (int64_t k = seg_len(sg) - 1; k >= 0 && rc == LW_OK; --k) {
+      rc = adjoint_step<T>(h, step_record<T>(aw, G, set_of(sg), k), f, fr, lg[cur], lg[cur ^ 1]);
       cur ^= 1;
     }
-    if (G.nseg > 1 && cudaEventRecord(rs.rev_done[set_of(sg)], s) != cudaSuccess) return LW_ECUDA;
+    if (rc != LW_OK) break;
+    if (G.nseg > 1 && cudaEventRecord(rs.rev_done[set_of(sg)], rs.rev) != cudaSuccess) {
+      rc = LW_ECUDA;
+      break;
+    }
   }
+  // back on the caller's stream, after the reverse sweep
+  h->stream = s;
+  if (cudaEventRecord(rs.join[1], rs.rev) != cudaSuccess || cudaStreamWaitEvent(s, rs.join[1], 0) != cudaSuccess)
+    return LW_ECUDA;
+  if (rc != LW_OK) return rc;
   // mu now holds lambda(c^0)
   launch(h, K_OTHER, [&] { lw::adj_vs_finish_kernel<<<1, 256, 0, s>>>(f.vs_part, nparts, f.lam_vs); });
   cudaMemcpyKind k = is_device_pointer(grad_c0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
