@@ -146,9 +146,9 @@ __global__ void __launch_bounds__(128) lbm_step_kernel(Args<T> a) {
 
 // D2Q9 specialisation of the fused collide-stream (same arithmetic as lbm_step_kernel):
 // 32-bit node offsets, the three source rows and columns hoisted, the wall test of
-// a row taken once per block (a block is one row segment), and streaming cache
-// hints on the population traffic (each population is touched once per step), so
-// that c and u stay in L2 for the transport kernel that follows.
+// a row taken once per block (a block is one row segment).  The population traffic
+// uses plain cached loads and stores: evict-first streaming hints on it were measured
+// 5 % slower (the odd step's shifted accesses reuse lines between neighbouring rows).
 template <typename T, int PARITY, bool RHO = false, bool SUGAR = false>
 __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, T* rho_out = nullptr);
 
@@ -203,10 +203,10 @@ __device__ __forceinline__ void d2q9_load(const Args<T>& a, const D2Q9Node& nd, 
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     if (PARITY == 0) {
-      g[i] = __ldcs(G + i * n + nd.node);
+      g[i] = __ldg(G + i * n + nd.node);
     } else {
-      g[i] = nd.behind_wall(i, -1) ? __ldcs(G + i * n + nd.node)
-                                   : __ldcs(G + D2Q9::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
+      g[i] = nd.behind_wall(i, -1) ? __ldg(G + i * n + nd.node)
+                                   : __ldg(G + D2Q9::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
     }
   }
 }
@@ -240,12 +240,12 @@ __device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9N
   const T om = a.omega, keep = T(1) - a.omega;
   auto store = [&](int i, T gs) {
     if (PARITY == 0) {
-      __stcs(G + D2Q9::opp(i) * n + node, gs);
+      G[D2Q9::opp(i) * n + node] = gs;
     } else {
       if (nd.behind_wall(i, +1))
-        __stcs(G + D2Q9::opp(i) * n + node, gs);
+        G[D2Q9::opp(i) * n + node] = gs;
       else
-        __stcs(G + i * n + (unsigned)((int)node + nd.off(i, +1)), gs);
+        G[i * n + (unsigned)((int)node + nd.off(i, +1))] = gs;
     }
   };
   // rest population
@@ -284,8 +284,8 @@ __device__ __forceinline__ void lbm_d2q9_body(const Args<T>& a, int bx, int by, 
 
 // D3Q19 specialisation (same arithmetic as lbm_step_kernel): 32-bit offsets with the
 // neighbour offsets along x, y (periodic) and z (walls or periodic) hoisted, the wall
-// tests taken once per block (a block is one x segment of one (y, z) row), streaming
-// cache hints on the population traffic.
+// tests taken once per block (a block is one x segment of one (y, z) row), plain cached
+// population traffic as in D2Q9.
 // One D3Q19 node's neighbour offsets (periodic x and y; z periodic or walled) and wall
 // flags.
 struct D3Q19Node {
@@ -329,10 +329,10 @@ __device__ __forceinline__ void d3q19_load(const Args<T>& a, const D3Q19Node& nd
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     if (PARITY == 0) {
-      g[i] = __ldcs(G + i * n + nd.node);
+      g[i] = __ldg(G + i * n + nd.node);
     } else {
-      g[i] = nd.behind_wall(i, -1) ? __ldcs(G + i * n + nd.node)
-                                   : __ldcs(G + D3Q19::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
+      g[i] = nd.behind_wall(i, -1) ? __ldg(G + i * n + nd.node)
+                                   : __ldg(G + D3Q19::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
     }
   }
 }
@@ -366,12 +366,12 @@ __device__ __forceinline__ void d3q19_collide_store(const Args<T>& a, const D3Q1
   const T om = a.omega, keep = T(1) - a.omega;
   auto store = [&](int i, T gs) {
     if (PARITY == 0) {
-      __stcs(G + D3Q19::opp(i) * n + node, gs);
+      G[D3Q19::opp(i) * n + node] = gs;
     } else {
       if (nd.behind_wall(i, +1))
-        __stcs(G + D3Q19::opp(i) * n + node, gs);
+        G[D3Q19::opp(i) * n + node] = gs;
       else
-        __stcs(G + i * n + (unsigned)((int)node + nd.off(i, +1)), gs);
+        G[i * n + (unsigned)((int)node + nd.off(i, +1))] = gs;
     }
   };
   {
