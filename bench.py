@@ -296,7 +296,7 @@ def bench_ours(args):
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     peak, peak_kind = load_peaks()
     step_ms = t_max / args.steps
-    # Algorithmic work per node (FP32; derivations in the design doc):
+    # Algorithmic work per node (FP32), counted on the textbook formulation:
     #   fluid kernel   2 Q 4 B populations in and out + 4 B c in (D2Q9 76 B, D3Q19 156 B)
     #   RK3 transport  3 stages x dim faces x (2 WENO5-JS reconstructions of 70 flop + split
     #                  fluxes, diffusion, sum) + divergence and Shu-Osher combination:
