@@ -2,7 +2,8 @@
 (FP32 populations as f - w_i, CUDA graphs, the default segment heights):
 
   * 2048 x 4096 D2Q9: three coupled steps of the whole lattice from the workload's initial
-    state against the FP64 oracle (relative L2 <= 1e-5 on c and u, deposit);
+    state against the FP64 oracle (relative L2 <= 1e-5 on c and u, deposit), for the default
+    workload and for its sugar, WENO3, sign-split and three-class variants;
   * 256 x 256 x 512 D3Q19: one step of the whole lattice.  The oracle computes a 32-level
     slab around the interface with a periodic vertical axis; one step moves information
     at most ten nodes (one for the fluid step, three per RK stage), so the levels more
@@ -30,8 +31,23 @@ def _lib():
 
 
 def _kw(wl):
-    return dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
-                settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity)
+    kw = dict(tau=wl.tau, gravity=wl.gravity, density_contrast=wl.density_contrast,
+              settling_velocity=wl.settling_velocity, diffusivity=wl.diffusivity, **wl.sugar, **wl.scheme)
+    if wl.class_vs:
+        kw["class_vs"] = wl.class_vs
+    return kw
+
+
+def _setup(sim, wl, to):
+    """Sugar and class fields of a workload (after init)."""
+    if wl.sugar:
+        sim.set_sugar(to(wl.initial_S()))
+    for k, ck in enumerate(wl.initial_classes() if wl.class_vs else []):
+        sim.set_class(k, to(ck))
+
+
+def _f32(a):
+    return a.astype(np.float32).astype(np.float64)
 
 
 def _run_gpu(wl, c0, steps, rows=0):
@@ -40,6 +56,7 @@ def _run_gpu(wl, c0, steps, rows=0):
     if rows:
         lw.lbm_wenoc_set_segment_rows(g.handle, rows)
     g.init(torch.from_numpy(c0.astype(np.float32)).cuda())
+    _setup(g, wl, lambda a: torch.from_numpy(a.astype(np.float32)).cuda())
     m0 = g.total_mass + g.deposit
     g.step(steps)
     return g, m0
@@ -50,15 +67,17 @@ def _u_ok(ug, uo):
     return du <= 1e-5 * np.linalg.norm(uo.ravel()) + 1e-12 * np.sqrt(uo.size)
 
 
-def test_d2q9_2048x4096_three_steps_whole_lattice():
-    wl = workloads.MAIN_2D
-    c0 = wl.initial_c().astype(np.float32).astype(np.float64)
+@pytest.mark.parametrize("wl", [workloads.MAIN_2D, workloads.SUGAR_2D, workloads.WENO3_2D,
+                                workloads.SIGN_SPLIT_2D, workloads.CLASSES_2D], ids=lambda w: w.name)
+def test_d2q9_2048x4096_three_steps_whole_lattice(wl):
+    c0 = _f32(wl.initial_c())
     g, m0 = _run_gpu(wl, c0, 3)
     _, ug, cg = (to_np(t) for t in g.fields())
     dep = g.deposit
-    assert (g.total_mass + dep) == pytest.approx(m0, rel=1e-6)
+    assert (g.total_mass + g.deposit) == pytest.approx(m0, rel=1e-6)
     o = oracle.OracleSim(wl.shape, **_kw(wl))
     o.init(c0)
+    _setup(o, wl, _f32)
     o.step(3)
     _, uo, co = o.fields()
     assert rel_l2(cg, co) <= 1e-5
