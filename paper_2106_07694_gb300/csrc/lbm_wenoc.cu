@@ -522,8 +522,8 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   cudaGetDevice(&h->device);
   h->sweep = !h->fp64 && !variant && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
-  // the row-sweep stage kernels take the scheme variants too, except with the sugar scalar
-  h->stage2d = !h->fp64 && !(variant && h->sugar) && h->p.dim == 2 && h->walls && !h->sweep &&
+  // the row-sweep stage kernels take the scheme variants and the sugar scalar too
+  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
                (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
   if (h->stage2d) {
     int sms = 0;
@@ -540,7 +540,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
       return LW_ECUDA;
     }
   }
-  h->sweep3d = !h->fp64 && !(variant && h->sugar) && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
+  h->sweep3d = !h->fp64 && h->p.dim == 3 && lw::sweep3d_supported(h->p.nz, h->walls);
   if (h->sweep3d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;

@@ -254,6 +254,24 @@ inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
   return min(2, ny);
 }
 
+// The stage kernel of the handle's transport scheme (runtime field) as a compile-time variant.
+template <int STAGE, bool SUGAR>
+inline void launch_stage2d_scheme(const Args<float>& a, const Stage2dParams& sp, dim3 grid, cudaStream_t s) {
+  switch (a.scheme) {
+    case kSchemeWeno3:
+      rk_stage2d_kernel<STAGE, SUGAR, kSchemeWeno3><<<grid, kS2T, 0, s>>>(a, sp);
+      break;
+    case kSchemeSignSplit:
+      rk_stage2d_kernel<STAGE, SUGAR, kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
+      break;
+    case kSchemeWeno3 | kSchemeSignSplit:
+      rk_stage2d_kernel<STAGE, SUGAR, kSchemeWeno3 | kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
+      break;
+    default:
+      rk_stage2d_kernel<STAGE, SUGAR><<<grid, kS2T, 0, s>>>(a, sp);
+  }
+}
+
 template <int STAGE>
 inline cudaError_t launch_stage2d(const Args<float>& a, const float* cin, float* cout, int H, cudaStream_t s) {
   Stage2dParams sp;
@@ -261,17 +279,10 @@ inline cudaError_t launch_stage2d(const Args<float>& a, const float* cin, float*
   sp.cout = cout;
   sp.H = H;
   const dim3 grid((a.nx + kS2T - 1) / kS2T, (a.ny + H - 1) / H);
-  // the scheme variants have no sugar instantiation (those handles take the generic path)
   if (a.S)
-    rk_stage2d_kernel<STAGE, true><<<grid, kS2T, 0, s>>>(a, sp);
-  else if (a.scheme == kSchemeWeno3)
-    rk_stage2d_kernel<STAGE, false, kSchemeWeno3><<<grid, kS2T, 0, s>>>(a, sp);
-  else if (a.scheme == kSchemeSignSplit)
-    rk_stage2d_kernel<STAGE, false, kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
-  else if (a.scheme == (kSchemeWeno3 | kSchemeSignSplit))
-    rk_stage2d_kernel<STAGE, false, kSchemeWeno3 | kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
+    launch_stage2d_scheme<STAGE, true>(a, sp, grid, s);
   else
-    rk_stage2d_kernel<STAGE><<<grid, kS2T, 0, s>>>(a, sp);
+    launch_stage2d_scheme<STAGE, false>(a, sp, grid, s);
   return cudaGetLastError();
 }
 

@@ -282,17 +282,21 @@ inline void (*sweep3d_entry())(Args<float>, Sweep3dParams) {
     return rk_sweep3d_kernel<STAGE, SUGAR, SCHEME>;
 }
 
-// The entry point of a stage for the handle's arguments (the scheme variants have no
-// sugar instantiation: those handles take the generic path).
+// The entry point of a stage for the handle's arguments: sugar and the transport scheme
+// (runtime fields) as compile-time variants.
+template <int STAGE, bool SUGAR>
+inline void (*sweep3d_entry_scheme(int scheme))(Args<float>, Sweep3dParams) {
+  switch (scheme) {
+    case kSchemeWeno3: return sweep3d_entry<STAGE, SUGAR, kSchemeWeno3>();
+    case kSchemeSignSplit: return sweep3d_entry<STAGE, SUGAR, kSchemeSignSplit>();
+    case kSchemeWeno3 | kSchemeSignSplit: return sweep3d_entry<STAGE, SUGAR, kSchemeWeno3 | kSchemeSignSplit>();
+    default: return sweep3d_entry<STAGE, SUGAR>();
+  }
+}
+
 template <int STAGE>
 inline void (*sweep3d_entry_for(const Args<float>& a))(Args<float>, Sweep3dParams) {
-  if (a.S) return sweep3d_entry<STAGE, true>();
-  switch (a.scheme) {
-    case kSchemeWeno3: return sweep3d_entry<STAGE, false, kSchemeWeno3>();
-    case kSchemeSignSplit: return sweep3d_entry<STAGE, false, kSchemeSignSplit>();
-    case kSchemeWeno3 | kSchemeSignSplit: return sweep3d_entry<STAGE, false, kSchemeWeno3 | kSchemeSignSplit>();
-    default: return sweep3d_entry<STAGE, false>();
-  }
+  return a.S ? sweep3d_entry_scheme<STAGE, true>(a.scheme) : sweep3d_entry_scheme<STAGE, false>(a.scheme);
 }
 
 inline size_t sweep3d_smem() { return sizeof(Sweep3dSmem); }
@@ -302,18 +306,15 @@ inline bool sweep3d_supported(int nz, bool walls) { return walls && nz >= 4; }
 inline cudaError_t sweep3d_prepare() {
   const int b = (int)sizeof(Sweep3dSmem);
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  void (*const entries[])(Args<float>, Sweep3dParams) = {
-      sweep3d_entry<1, false>(), sweep3d_entry<2, false>(), sweep3d_entry<3, false>(),
-      sweep3d_entry<1, true>(), sweep3d_entry<2, true>(), sweep3d_entry<3, true>(),
-      sweep3d_entry<1, false, kSchemeWeno3>(), sweep3d_entry<2, false, kSchemeWeno3>(),
-      sweep3d_entry<3, false, kSchemeWeno3>(), sweep3d_entry<1, false, kSchemeSignSplit>(),
-      sweep3d_entry<2, false, kSchemeSignSplit>(), sweep3d_entry<3, false, kSchemeSignSplit>(),
-      sweep3d_entry<1, false, kSchemeWeno3 | kSchemeSignSplit>(),
-      sweep3d_entry<2, false, kSchemeWeno3 | kSchemeSignSplit>(),
-      sweep3d_entry<3, false, kSchemeWeno3 | kSchemeSignSplit>()};
   cudaError_t e = cudaSuccess;
-  for (auto f : entries)
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, at, b);
+  for (int scheme = 0; scheme < 4; ++scheme) {  // every stage x sugar x scheme entry point
+    void (*const entries[])(Args<float>, Sweep3dParams) = {
+        sweep3d_entry_scheme<1, false>(scheme), sweep3d_entry_scheme<2, false>(scheme),
+        sweep3d_entry_scheme<3, false>(scheme), sweep3d_entry_scheme<1, true>(scheme),
+        sweep3d_entry_scheme<2, true>(scheme), sweep3d_entry_scheme<3, true>(scheme)};
+    for (auto f : entries)
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, at, b);
+  }
   return e;
 }
 

@@ -128,6 +128,29 @@ def test_variant_with_sugar_matches_oracle():
     assert rel_l2(to_np(g.sugar()), o.sugar()) <= 1e-12
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("shape", [(132, 64), (36, 20, 40)])
+def test_variant_with_sugar_fp32_sweep_kernels(variant, shape):
+    """The variants combined with the sugar scalar on the FP32 row-sweep (2D) and z-sweep (3D)
+    stage kernels, against the oracle to 1e-5 (c, u, S)."""
+    from paper_2106_07694_gb300.lbm_wenoc import Simulation
+    c0 = workloads.interface_field(shape, interface_frac=0.5, amplitude=0.02, seed=13).astype(np.float32)
+    S0 = (1.0 - workloads.interface_field(shape, interface_frac=0.5, amplitude=0.0, seed=13)).astype(np.float32)
+    c0, S0 = c0.astype(np.float64), S0.astype(np.float64)
+    kw = dict(STRONG, sugar=True, sugar_contrast=0.5, sugar_diffusivity=0.02, phi0=0.05, vs_sugar=0.3, **variant)
+    g = Simulation(shape, fp64=False, **kw)
+    g.init(c0)
+    g.set_sugar(S0)
+    o = oracle.OracleSim(shape, **kw)
+    o.init(c0)
+    o.set_sugar(S0)
+    steps = 20 if len(shape) == 2 else 8
+    g.step(steps)
+    o.step(steps)
+    _check(g, o, 1e-5, 1e-12)
+    assert rel_l2(to_np(g.sugar()), o.sugar()) <= 1e-5
+
+
 def test_variant_errors():
     from paper_2106_07694_gb300 import lbm_wenoc as lw
     for variant in VARIANTS:
