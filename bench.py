@@ -143,10 +143,10 @@ _CSRC = "paper_2106_07694_gb300/csrc/"
 _LBM_SRC = ("lbm_kernels.cuh", "lattice.cuh", "common.cuh")
 _STAGE_SRC = ("transport_stage2d.cuh", "transport_sweep2d.cuh", "reduce_kernels.cuh", "common.cuh")
 NCU_TRAFFIC = {
-    "lbm_collide_stream": (643.11e6, _LBM_SRC, "916b01ee7eb7"),
-    "rk_stage1": (113.11e6, _STAGE_SRC, "530c7104184c"),
-    "rk_stage2": (150.60e6, _STAGE_SRC, "530c7104184c"),
-    "rk_stage3": (146.76e6, _STAGE_SRC, "530c7104184c"),
+    "lbm_collide_stream": (643.15e6, _LBM_SRC, "916b01ee7eb7"),
+    "rk_stage1": (112.97e6, _STAGE_SRC, "a94c5aff49b3"),
+    "rk_stage2": (150.55e6, _STAGE_SRC, "a94c5aff49b3"),
+    "rk_stage3": (146.62e6, _STAGE_SRC, "a94c5aff49b3"),
     # 512 x 1024 adjoint workload (the face records stay in L2)
     "adj_faces": (8.61e6, ("adjoint.cuh",) + _LBM_SRC, "66654c95daaa"),
 }
