@@ -321,9 +321,10 @@ inline cudaError_t sweep3d_prepare() {
 inline int sweep3d_rows(int nx, int ny, int nz, int sm_count, int override_rows) {
   if (override_rows > 0) return min(override_rows, nz);
   const long long tiles = (long long)((nx + kT3x - 1) / kT3x) * ((ny + kT3y - 1) / kT3y);
-  // at least sixteen CTAs per SM in total (four waves at four resident CTAs per SM),
-  // segments no shorter than 24 levels
-  long long segs = (16LL * sm_count + tiles - 1) / tiles;
+  // at least 21 CTAs per SM in total (five waves at four resident CTAs per SM: on the
+  // 256 x 256 x 512 lattice 40-level segments, 0.6 % faster than 52), segments no shorter
+  // than 24 levels
+  long long segs = (21LL * sm_count + tiles - 1) / tiles;
   int H = (int)((nz + segs - 1) / segs);
   return max(min(24, nz), H);
 }
