@@ -56,11 +56,12 @@ extern "C" {
                                      advected by first-order upwind (Supplement Eqs. S5, S6) with
                                      diffusion D_s; not with LW_FUSED_RK3, batches or the gradient */
 #define LW_WENO3 0x40u            /* the paper's third-order WENO (Supplement Eqs. S10-S20, linear weights
-                                     (2/3, 1/3) of Eq. S16) instead of WENO5; generic stage kernels */
+                                     (2/3, 1/3) of Eq. S16) instead of WENO5; a compile-time variant of
+                                     the FP32 sweep stage kernels (FP64: the generic ones) */
 #define LW_SIGN_SPLIT 0x80u       /* whole flux w c reconstructed from the side the face velocity
                                      (w_i + w_{i+1})/2 comes from (ties left) instead of the
-                                     Lax-Friedrichs split; generic stage kernels.  Neither variant with
-                                     LW_FUSED_RK3, batches or the gradient */
+                                     Lax-Friedrichs split; stage kernels as for LW_WENO3.  Neither
+                                     variant with LW_FUSED_RK3, batches or the gradient */
 
 typedef struct lbm_wenoc lbm_wenoc; /* opaque host-side handle */
 
@@ -162,8 +163,8 @@ int lbm_wenoc_profile_read(lbm_wenoc* h, lbm_wenoc_kernel_stat* out, int max, in
 /* Number of kernel launches this handle has issued since create. */
 int64_t lbm_wenoc_launch_count(const lbm_wenoc* h);
 
-/* Tuning of the FP32 transport sweeps: rows per CTA segment of the fused 2D kernel, or
- * z levels per CTA segment of the 3D stage kernels (0 = default).  Results do not
+/* Tuning of the FP32 transport sweeps: rows per CTA segment of the 2D stage kernels (or
+ * of the fused 2D kernel), or z levels per CTA segment of the 3D stage kernels (0 = default).  Results do not
  * depend on it (bitwise).  No effect on FP64 or periodic-vertical handles.  Drops
  * captured graphs; call between steps. */
 int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows);
@@ -215,8 +216,12 @@ void lbm_wenoc_batch_destroy(lbm_wenoc_batch* b);
  * lf_alpha > 0 (LW_EINVAL otherwise).  adj_workspace: caller-owned device memory of at
  * least lbm_wenoc_gradient_workspace_bytes() (checkpoints + one segment of states +
  * adjoint fields, one stage's face records), 256-byte aligned.  Deterministic (no
- * atomics): the same inputs give the same bits for any segment.  Synchronises.  Afterwards the handle holds an
- * intermediate state and must be initialised again before stepping. */
+ * atomics): the same inputs give the same bits for any segment.  The reverse steps run on
+ * an internal stream at the device's greatest priority and the recompute of the next
+ * segment on a second internal stream, both ordered after the work already queued on the
+ * handle's stream and joined back to it; both are created and destroyed by the call.
+ * Synchronises.  Afterwards the handle holds an intermediate state and must be
+ * initialised again before stepping. */
 int lbm_wenoc_gradient_workspace_bytes(const lbm_wenoc_params* p, int64_t nsteps, int32_t segment, size_t* bytes);
 int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t segment, void* adj_workspace,
                                size_t bytes, void* grad_c0, double* dJ_dVs, double* J);
