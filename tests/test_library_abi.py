@@ -36,6 +36,21 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as C99 on its own (no C++ or CUDA types leak into it)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "lbm_wenoc.h"\nint main(void) { lbm_wenoc_params p = {0}; '
+                   'size_t b = 0; return lbm_wenoc_workspace_bytes(&p, &b) == LW_OK; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_symbols():
         assert hasattr(lib, name), name
