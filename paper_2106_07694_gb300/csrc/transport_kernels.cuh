@@ -201,30 +201,32 @@ __global__ void __launch_bounds__(128) rk_stage_kernel(Args<T> a) {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) sugar_kernel(Args<T> a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  const int z = blockIdx.z;
-  if (x >= a.nx) return;
-  const int VA = DIM - 1;
-  const long long node = ((long long)z * a.ny + y) * a.nx + x;
-  const int pos[3] = {x, y, z};
-  const int ext[3] = {a.nx, a.ny, a.nz};
-  const long long stride[3] = {1, a.nx, (long long)a.nx * a.ny};
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  if (x >= nx) return;
+  const bool walls = a.walls != 0;
+  const unsigned n = (unsigned)a.n;  // Q n < 2^31 (checked at create)
+  const unsigned node = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+  // neighbour offsets along each axis: x (and y in 3D) periodic; the vertical axis wraps, or
+  // at a wall takes offset 0 (the ghost mirrors the boundary node: no flux through the wall)
+  int off_m[3] = {x == 0 ? nx - 1 : -1, 0, 0}, off_p[3] = {x == nx - 1 ? -(nx - 1) : 1, 0, 0};
+  if (DIM == 2) {
+    off_m[1] = y == 0 ? (walls ? 0 : (ny - 1) * nx) : -nx;
+    off_p[1] = y == ny - 1 ? (walls ? 0 : -(ny - 1) * nx) : nx;
+  } else {
+    const int plane = nx * ny;
+    off_m[1] = y == 0 ? (ny - 1) * nx : -nx;
+    off_p[1] = y == ny - 1 ? -(ny - 1) * nx : nx;
+    off_m[2] = z == 0 ? (walls ? 0 : (nz - 1) * plane) : -plane;
+    off_p[2] = z == nz - 1 ? (walls ? 0 : -(nz - 1) * plane) : plane;
+  }
   const T s0 = a.S[node];
   T next = s0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const bool wall_axis = (d == VA) && a.walls;
-    int pm = pos[d] - 1, pp = pos[d] + 1;
-    if (wall_axis) {
-      pm = pm < 0 ? 0 : pm;                       // mirror ghost below the floor
-      pp = pp >= ext[d] ? ext[d] - 1 : pp;        // and above the lid
-    } else {
-      pm = wrap_any(pm, ext[d]);
-      pp = wrap_any(pp, ext[d]);
-    }
-    const T sm = a.S[node + (long long)(pm - pos[d]) * stride[d]];
-    const T sp = a.S[node + (long long)(pp - pos[d]) * stride[d]];
-    const T u = a.u[(long long)d * a.n + node];
+    const T sm = a.S[(unsigned)((int)node + off_m[d])];
+    const T sp = a.S[(unsigned)((int)node + off_p[d])];
+    const T u = a.u[(unsigned)d * n + node];
     next -= u > T(0) ? u * (s0 - sm) : u * (sp - s0);
     next += a.Ds * (sp - T(2) * s0 + sm);
   }
