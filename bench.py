@@ -54,10 +54,19 @@ UNIT = "GLUPS"
 ADJ_FACES_FLOP = 766
 
 
-def fp32_peak_tflops(clk):
-    """FP32 ALU peak derived from the unit counts: 152 SMs x 128 lanes x 2 flop x SM clock."""
+def sm_count(dev=None):
+    """Streaming multiprocessors of the device (152 on a GB300)."""
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(dev if dev is not None else 0).multi_processor_count)
+    except Exception:
+        return 152
+
+
+def fp32_peak_tflops(clk, sms=None):
+    """FP32 ALU peak derived from the unit counts: SMs x 128 lanes x 2 flop x SM clock."""
     sm_hz = ((clk or {}).get("sm_mhz") or 2070.0) * 1e6
-    return 152 * 128 * 2 * sm_hz / 1e12
+    return (sms or sm_count()) * 128 * 2 * sm_hz / 1e12
 
 
 def phys_kwargs(wl):
@@ -84,7 +93,9 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons: one reading right before the timed region,
+    samples every 200 ms during it, one reading right after it (a short region still gets
+    two readings)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -94,7 +105,16 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
+    def _once(self):
+        try:
+            out = subprocess.run(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                  "-i", str(self.dev)], capture_output=True, text=True, timeout=10).stdout
+            self.lines.extend(ln.strip() for ln in out.splitlines() if ln.strip())
+        except Exception:
+            pass
+
     def start(self):
+        self._once()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
@@ -109,14 +129,16 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.t.join(timeout=2)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        self._once()
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -141,7 +163,8 @@ class ClockSampler:
 # changed kernel reports null until it is captured again.
 _CSRC = "paper_2106_07694_gb300/csrc/"
 _LBM_SRC = ("lbm_kernels.cuh", "lattice.cuh", "common.cuh")
-_STAGE_SRC = ("transport_stage2d.cuh", "transport_sweep2d.cuh", "reduce_kernels.cuh", "common.cuh")
+_STAGE_SRC = ("transport_stage2d_wide.cuh", "transport_stage2d.cuh", "transport_sweep2d.cuh", "reduce_kernels.cuh",
+              "common.cuh")
 NCU_TRAFFIC = {
     "lbm_collide_stream": (643.15e6, _LBM_SRC, "916b01ee7eb7"),
     "rk_stage1": (112.97e6, _STAGE_SRC, "a94c5aff49b3"),
@@ -302,7 +325,7 @@ def bench_ours(args):
     #                  fluxes, diffusion, sum) + divergence and Shu-Osher combination:
     #                  915 flop in 2D, 1371 flop in 3D (a third per stage kernel)
     #   whole step     populations in and out + c in and out: 80 B (2D), 160 B (3D)
-    # FP32 peak: 152 SMs x 128 lanes x 2 flop (FMA) x the sampled SM clock.
+    # FP32 peak: SMs x 128 lanes x 2 flop (FMA) x the sampled SM clock.
     dim = len(wl.shape)
     es = 8 if fp64 else 4
     lbm_B = 2 * (9 if dim == 2 else 19) * es + es + (es if wl.sugar else 0)  # + S in (sugar force)
@@ -319,8 +342,8 @@ def bench_ours(args):
     step_B += 2 * es * (ncls - 1)  # every class's c in and out
     flop_of = {"rk3_sweep2d": tr_flop, "rk3_sweep3d": tr_flop, "rk_stage1": tr_flop / 3,
                "rk_stage2": tr_flop / 3, "rk_stage3": tr_flop / 3}
-    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
-    fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
+    sms = sm_count(dev)
+    fp32_peak = fp32_peak_tflops(clk, sms)
     # ncu traffic was captured on the plain 2D workload's kernels only
     ncu_traffic = {k: kernel_traffic(k) if wl is workloads.MAIN_2D else None for k in NCU_TRAFFIC}
 
@@ -331,7 +354,7 @@ def bench_ours(args):
     if dominant in flop_of:
         achieved = flop_of[dominant] * wl.nodes / avg_s(dominant) / 1e12
         roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak,
-                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sampled SM clock",
+                    "peak_source": f"derived: {sms} SM x 128 FP32 lanes x 2 x sampled SM clock",
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": ncu_traffic.get(dominant),
                     "alg_flop_per_node": flop_of[dominant]}
     elif dominant == "lbm_collide_stream":
@@ -365,6 +388,10 @@ def bench_ours(args):
     step_roofline = {"bound": "hbm", "alg_bytes_per_node": step_B,
                      "achieved": step_B * wl.nodes / (step_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": step_B * wl.nodes / (step_ms * 1e-3) / 1e9 / peak}
+    if roofline and roofline.get("bound"):  # the whole coupled step beside the dominant kernel
+        roofline["step_frac"] = step_roofline["frac"]
+        roofline["step_achieved_gbs"] = step_roofline["achieved"]
+        roofline["step_alg_bytes_per_node"] = step_B
 
     # ---- end to end through the C ABI with host buffers: H2D of c0 (pinned), init,
     # K steps, deposit read and D2H of the final c field, all inside the timed region
@@ -603,7 +630,7 @@ def bench_adjoint(args):
             "kernel": "adj_faces", "bound": "alu", "alg_flop_per_node": ADJ_FACES_FLOP,
             "achieved": ADJ_FACES_FLOP * nodes / (faces_us * 1e-6) / 1e12, "peak": peak_alu,
             "unit": "TFLOP/s", "frac": ADJ_FACES_FLOP * nodes / (faces_us * 1e-6) / 1e12 / peak_alu,
-            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sampled SM clock",
+            "peak_source": f"derived: {sm_count()} SM x 128 FP32 lanes x 2 x sampled SM clock",
             "traffic": kernel_traffic("adj_faces")},
         "e2e": {"value": nodes * nsteps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * nodes / nsteps,
                 "d2h_bytes_per_step": (4 * nodes + 8) / nsteps},

@@ -62,6 +62,9 @@ extern "C" {
                                      (w_i + w_{i+1})/2 comes from (ties left) instead of the
                                      Lax-Friedrichs split; stage kernels as for LW_WENO3.  Neither
                                      variant with LW_FUSED_RK3, batches or the gradient */
+#define LW_ONE_COLUMN 0x100u      /* 2D FP32: the row-sweep stage kernels with one column per thread
+                                     instead of four (bitwise the same c and u; the deposit's FP64
+                                     partial sums are grouped differently).  For comparisons */
 
 typedef struct lbm_wenoc lbm_wenoc; /* opaque host-side handle */
 
@@ -77,7 +80,7 @@ typedef struct {
   double u_cap;              /* bound on |u_d| checked on the device; 0 selects 0.1 */
   double body_force[3];      /* extra uniform force (e.g. a channel flow), added to the buoyancy */
   uint32_t flags;            /* LW_FP64 | LW_PERIODIC_VERTICAL | LW_FROZEN_VELOCITY | LW_NO_GRAPH | LW_FUSED_RK3
-                                | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT */
+                                | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT | LW_ONE_COLUMN */
   /* used with LW_SUGAR only (S normalised by its lower-layer value S0) */
   double sugar_contrast;     /* S* = rho(S0)/rho_0 - 1 (Eq. S_star): force -gravity*S* S (1 - phi0 c) e_v */
   double sugar_diffusivity;  /* D_s >= 0 */

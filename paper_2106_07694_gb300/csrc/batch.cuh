@@ -10,7 +10,7 @@
 #pragma once
 #include "common.cuh"
 #include "lbm_kernels.cuh"
-#include "transport_stage2d.cuh"
+#include "transport_stage2d_wide.cuh"
 
 namespace lw {
 
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(128) lbm_d2q9_batch_kernel(BatchTables t) {
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(kS2T) stage2d_batch_kernel(BatchTables t) {
+__global__ void __launch_bounds__(kWT) stage2d_batch_kernel(BatchTables t) {
   __shared__ Args<float> sa;
   __shared__ int s_meta[4];
   if (threadIdx.x == 0) {
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kS2T) stage2d_batch_kernel(BatchTables t) {
   sp.cin = STAGE == 1 ? sa.c : (STAGE == 2 ? sa.c1 : sa.c2);
   sp.cout = STAGE == 1 ? sa.c1 : (STAGE == 2 ? sa.c2 : sa.c);
   sp.H = s_meta[3];
-  stage2d_body<STAGE>(sa, sp, s_meta[0], s_meta[1], s_meta[2]);
+  stage2d_wide_body<STAGE>(sa, sp, s_meta[0], s_meta[1], s_meta[2]);
 }
 
 }  // namespace lw

@@ -21,6 +21,7 @@
 #include "transport_sweep2d.cuh"
 #include "transport_sweep3d.cuh"
 #include "transport_stage2d.cuh"
+#include "transport_stage2d_wide.cuh"
 #include "batch.cuh"
 #include "adjoint.cuh"
 
@@ -136,6 +137,8 @@ struct lbm_wenoc {
   int sweep3d_rows = 0;
   bool stage2d = false;  // 2D FP32 with walls: three row-sweep stage kernels
   int stage2d_rows = 0;
+  bool wide = false;     // ... with four columns per thread (default scheme, no sugar)
+  int wide_per_sm = 1;   // CTAs of the four-column stage kernel one SM holds at once
   bool initialised = false;
   bool sugar = false;  // LW_SUGAR: S in L.sa / L.sb, selected by cur (the generic transport path)
   int ncls = 1;        // particle classes
@@ -355,6 +358,12 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
   if (std::is_same<T, float>::value && LAT::DIM == 2 && h->stage2d) {
     const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
     const int H = h->stage2d_rows;
+    if (h->wide) {
+      launch(h, K_STAGE1, [&] { lw::launch_stage2d_wide<1>(af, af.c, af.c1, H, s); });
+      launch(h, K_STAGE2, [&] { lw::launch_stage2d_wide<2>(af, af.c1, af.c2, H, s); });
+      launch(h, K_STAGE3, [&] { lw::launch_stage2d_wide<3>(af, af.c2, af.c, H, s); });  // + deposit
+      return;
+    }
     launch(h, K_STAGE1, [&] { lw::launch_stage2d<1>(af, af.c, af.c1, H, s); });
     launch(h, K_STAGE2, [&] { lw::launch_stage2d<2>(af, af.c1, af.c2, H, s); });
     launch(h, K_STAGE3, [&] { lw::launch_stage2d<3>(af, af.c2, af.c, H, s); });  // + deposit
@@ -525,10 +534,21 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   // the row-sweep stage kernels take the scheme variants and the sugar scalar too
   h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
                (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
+  h->wide = h->stage2d && !h->sugar && !variant && !(p->flags & LW_ONE_COLUMN);
   if (h->stage2d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
-    h->stage2d_rows = lw::stage2d_rows(p->nx, p->ny, sms, 0);
+    if (h->wide) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lw::rk_stage2d_wide_kernel<3>, lw::kWT, 0) !=
+              cudaSuccess ||
+          per_sm <= 0)
+        per_sm = 1;
+      h->wide_per_sm = per_sm;
+      h->stage2d_rows = lw::stage2d_wide_rows(p->nx, p->ny, sms, per_sm, 0);
+    } else {
+      h->stage2d_rows = lw::stage2d_rows(p->nx, p->ny, sms, 0);
+    }
   }
   if (h->sweep) {
     int sms = 0;
@@ -854,7 +874,9 @@ int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
     destroy_graphs(h);
     if (h->sweep3d) h->sweep3d_rows = lw::sweep3d_rows(h->p.nx, h->p.ny, h->p.nz, sms, rows);
-    if (h->stage2d) h->stage2d_rows = lw::stage2d_rows(h->p.nx, h->p.ny, sms, rows);
+    if (h->stage2d)
+      h->stage2d_rows = h->wide ? lw::stage2d_wide_rows(h->p.nx, h->p.ny, sms, h->wide_per_sm, rows)
+                                : lw::stage2d_rows(h->p.nx, h->p.ny, sms, rows);
     return LW_OK;
   }
   if (!h->sweep) return LW_OK;
@@ -903,7 +925,7 @@ namespace {
 bool batch_params_ok(const lbm_wenoc_params& p) {
   return check_params(&p) == LW_OK && p.dim == 2 && !(p.flags & LW_FP64) && !(p.flags & LW_PERIODIC_VERTICAL) &&
          !(p.flags & (LW_FROZEN_VELOCITY | LW_FUSED_RK3 | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT)) && p.n_classes < 2 &&
-         (p.nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
+         (p.nx + lw::kWW - 1) / lw::kWW <= lw::kMaxReduceBlocks;
 }
 
 size_t batch_tables_bytes(int count) {
@@ -932,8 +954,8 @@ int batch_upload_tables(lbm_wenoc_batch* b) {
     args[i] = make_args<float>(h);
     lgx[i] = (h->p.nx + kLbmThreads - 1) / kLbmThreads;
     lstart[i + 1] = lstart[i] + lgx[i] * h->p.ny;
-    sstrips[i] = (h->p.nx + lw::kS2T - 1) / lw::kS2T;
-    srows[i] = b->rows > 0 ? std::min(b->rows, h->p.ny) : h->stage2d_rows;
+    sstrips[i] = (h->p.nx + lw::kWW - 1) / lw::kWW;
+    srows[i] = b->rows > 0 ? std::min(std::min(b->rows, h->p.ny), lw::kWmaxH) : h->stage2d_rows;
     const int segs = (h->p.ny + srows[i] - 1) / srows[i];
     sstart[i + 1] = sstart[i] + sstrips[i] * segs;
   }
@@ -968,9 +990,9 @@ void batch_enqueue(lbm_wenoc_batch* b, cudaStream_t s, int parity) {
     lw::lbm_d2q9_batch_kernel<0><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
   else
     lw::lbm_d2q9_batch_kernel<1><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
-  lw::stage2d_batch_kernel<1><<<b->st_blocks, lw::kS2T, 0, s>>>(t);
-  lw::stage2d_batch_kernel<2><<<b->st_blocks, lw::kS2T, 0, s>>>(t);
-  lw::stage2d_batch_kernel<3><<<b->st_blocks, lw::kS2T, 0, s>>>(t);
+  lw::stage2d_batch_kernel<1><<<b->st_blocks, lw::kWT, 0, s>>>(t);
+  lw::stage2d_batch_kernel<2><<<b->st_blocks, lw::kWT, 0, s>>>(t);
+  lw::stage2d_batch_kernel<3><<<b->st_blocks, lw::kWT, 0, s>>>(t);
 }
 
 int batch_capture(lbm_wenoc_batch* b, int parity, int count, cudaGraphExec_t* out) {

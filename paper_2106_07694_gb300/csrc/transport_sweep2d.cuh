@@ -46,9 +46,13 @@ namespace lw {
 //   q-weights  A1 A2,  6 A0 A2,  3 A0 A1;
 //   numerator  A1 (A2 r0 + 3 A0 r2) + 6 A0 A2 r1,  denominator  A1 (A2 + 3 A0) + 6 A0 A2.
 // Returns the face value c + sum_k w_k (q_k - c).
-__device__ __forceinline__ float weno5_face_value(float a, float b, float c, float d, float e) {
-  const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
-  const float s0 = d2 - d1, s1 = d3 - d2, s2 = d4 - d3;
+//
+// weno5_q takes the differences d1..d4 and the second differences s_k = d_{k+2} - d_{k+1}
+// and returns 6 sum_k w_k (q_k - c) = num / den, so that kernels which reconstruct several
+// adjacent faces can share the differences between them.  Rounding is sign-symmetric, so
+// b - a = -(a - b) bit for bit: a mirrored (h-) reconstruction may pass the negated
+// differences of the stored order and gets the same bits as weno5_face_value.
+__device__ __forceinline__ float weno5_q(float d1, float d2, float d3, float d4, float s0, float s1, float s2) {
   const float t0 = fmaf(3.f, d2, -d1), t1 = d2 + d3, t2 = fmaf(-3.f, d3, d4);
   const float q = 3.f / 13.f, eps = 1e-6f * (12.f / 13.f);
   float A0 = fmaf(s0, s0, fmaf(q * t0, t0, eps));
@@ -61,7 +65,12 @@ __device__ __forceinline__ float weno5_face_value(float a, float b, float c, flo
   const float A02x6 = 6.f * (A0 * A2);
   const float num = fmaf(A1, fmaf(3.f * A0, r2, A2 * r0), A02x6 * r1);
   const float den = fmaf(A1, fmaf(3.f, A0, A2), A02x6);
-  return fmaf(__fdividef(num, den), 1.f / 6.f, c);
+  return __fdividef(num, den);
+}
+
+__device__ __forceinline__ float weno5_face_value(float a, float b, float c, float d, float e) {
+  const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
+  return fmaf(weno5_q(d1, d2, d3, d4, d2 - d1, d3 - d2, d4 - d3), 1.f / 6.f, c);
 }
 
 // The paper's third-order WENO face value (Supplement Eqs. S10, S11, S14-S16) on the

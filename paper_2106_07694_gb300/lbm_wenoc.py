@@ -29,6 +29,7 @@ LW_FUSED_RK3 = 0x10
 LW_SUGAR = 0x20
 LW_WENO3 = 0x40
 LW_SIGN_SPLIT = 0x80
+LW_ONE_COLUMN = 0x100
 
 _ERRORS = {LW_EINVAL: "LW_EINVAL", LW_ENOMEM: "LW_ENOMEM", LW_ECUDA: "LW_ECUDA",
            LW_EUNSTABLE: "LW_EUNSTABLE", LW_ETIMEOUT: "LW_ETIMEOUT", LW_ESTATE: "LW_ESTATE"}
@@ -299,7 +300,7 @@ def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velo
                 diffusivity=0.0, lf_alpha=0.0, u_cap=0.0, body_force=(0.0, 0.0, 0.0), fp64=False,
                 periodic_vertical=False, frozen_velocity=False, graphs=True, fused_rk3=False,
                 sugar=False, sugar_contrast=0.0, sugar_diffusivity=0.0, phi0=0.0, vs_sugar=0.0,
-                weno3=False, sign_split=False, class_vs=()):
+                weno3=False, sign_split=False, class_vs=(), one_column=False):
     p = lbm_wenoc_params()
     p.dim = len(shape)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -311,7 +312,7 @@ def make_params(shape, tau=0.6, gravity=0.0, density_contrast=1.0, settling_velo
     p.flags = ((LW_FP64 if fp64 else 0) | (LW_PERIODIC_VERTICAL if periodic_vertical else 0) |
                (LW_FROZEN_VELOCITY if frozen_velocity else 0) | (0 if graphs else LW_NO_GRAPH) |
                (LW_FUSED_RK3 if fused_rk3 else 0) | (LW_SUGAR if sugar else 0) | (LW_WENO3 if weno3 else 0) |
-               (LW_SIGN_SPLIT if sign_split else 0))
+               (LW_SIGN_SPLIT if sign_split else 0) | (LW_ONE_COLUMN if one_column else 0))
     p.sugar_contrast, p.sugar_diffusivity, p.phi0, p.vs_sugar = sugar_contrast, sugar_diffusivity, phi0, vs_sugar
     p.n_classes = len(class_vs)
     for k, v in enumerate(class_vs):
