@@ -42,6 +42,20 @@ struct Args {
   int scheme;  // flux variant bits (kSchemeWeno3, kSchemeSignSplit); 0 = WENO5, Lax-Friedrichs
 };
 
+// Global-load policies.  LoadNC reads through the non-coherent (read-only) path, for data
+// no thread writes while the kernel runs; LoadCoherent issues plain loads, for kernels
+// that read what other CTAs wrote earlier in the same launch (after a grid barrier).
+struct LoadNC {
+  static __device__ __forceinline__ float s(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ double s(const double* p) { return __ldg(p); }
+  static __device__ __forceinline__ float4 v4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+};
+struct LoadCoherent {
+  static __device__ __forceinline__ float s(const float* p) { return *p; }
+  static __device__ __forceinline__ double s(const double* p) { return *p; }
+  static __device__ __forceinline__ float4 v4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+};
+
 constexpr int kSchemeWeno3 = 1;
 constexpr int kSchemeSignSplit = 2;
 

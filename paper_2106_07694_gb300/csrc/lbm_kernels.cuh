@@ -196,17 +196,17 @@ __device__ __forceinline__ D2Q9Node d2q9_node(const Args<T>& a, int x, int y) {
 }
 
 // The node's populations as they stand at the start of a step of this parity (AA pattern).
-template <typename T, int PARITY>
+template <typename T, int PARITY, class LD = LoadNC>
 __device__ __forceinline__ void d2q9_load(const Args<T>& a, const D2Q9Node& nd, T (&g)[9]) {
   const unsigned n = (unsigned)a.n;
   const T* __restrict__ G = a.g;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     if (PARITY == 0) {
-      g[i] = __ldg(G + i * n + nd.node);
+      g[i] = LD::s(G + i * n + nd.node);
     } else {
-      g[i] = nd.behind_wall(i, -1) ? __ldg(G + i * n + nd.node)
-                                   : __ldg(G + D2Q9::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
+      g[i] = nd.behind_wall(i, -1) ? LD::s(G + i * n + nd.node)
+                                   : LD::s(G + D2Q9::opp(i) * n + (unsigned)((int)nd.node + nd.off(i, -1)));
     }
   }
 }

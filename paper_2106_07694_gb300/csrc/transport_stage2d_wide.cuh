@@ -31,6 +31,7 @@ constexpr int kWW = kWq * kWT;   // columns per strip
 constexpr int kWQ = kWT + 2;     // staged quads per row: the strip and one halo quad per side
 constexpr int kWring = 6;        // y ring rows (k-2 .. k+3)
 constexpr int kWmaxH = 64;       // longest row segment (its strip-edge faces are held in smem)
+constexpr int kWminB = 1;        // CTAs per SM the register allocation must allow
 
 struct StageWideSmem {
   float4 xp[2][kWQ];  // x-split h+/alpha of the staged row, by row parity
@@ -44,8 +45,6 @@ struct StageWideSmem {
   bool last;
 };
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-
 // Lax-Friedrichs split of one node: p = h+/alpha, m = h-/alpha with h = c/2, w = u/alpha.
 __device__ __forceinline__ void lf_split(float c, float w, float& p, float& m) {
   const float h = 0.5f * c;
@@ -53,7 +52,9 @@ __device__ __forceinline__ void lf_split(float c, float w, float& p, float& m) {
   m = fmaf(w, h, -h);
 }
 
-template <int STAGE>
+// LD: the global-load policy (LoadNC for a launch of its own, LoadCoherent inside a kernel
+// whose earlier phases wrote the fields).
+template <int STAGE, class LD = LoadNC>
 __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const Stage2dParams& sp, int bx, int by,
                                                   int strips) {
   __shared__ __align__(16) StageWideSmem S;
@@ -77,11 +78,11 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
   float4 Xc, Xu, Hc = make_float4(0.f, 0.f, 0.f, 0.f), Hu = Hc;
   auto fetch_x = [&](int r) {
     const unsigned row = (unsigned)r * (unsigned)nx;
-    Xc = ldg4(cin + row + X);
-    Xu = ldg4(ux + row + X);
+    Xc = LD::v4(cin + row + X);
+    Xu = LD::v4(ux + row + X);
     if (halo) {
-      Hc = ldg4(cin + row + hX);
-      Hu = ldg4(ux + row + hX);
+      Hc = LD::v4(cin + row + hX);
+      Hu = LD::v4(ux + row + hX);
     }
   };
   auto put_quad = [&](int b, int q, const float4& c, const float4& u) {
@@ -108,8 +109,8 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
     int lr = l < 0 ? -1 - l : (l >= ny ? 2 * ny - 1 - l : l);
     lr = max(0, min(ny - 1, lr));
     const unsigned row = (unsigned)lr * (unsigned)nx;
-    Rc = ldg4(cin + row + X);
-    Ru = ldg4(uy + row + X);
+    Rc = LD::v4(cin + row + X);
+    Ru = LD::v4(uy + row + X);
   };
   // ring entries are addressed by byte offset (slot * kWT + t) * 16, rotated as the sweep advances
   auto ring_at = [&](float4 (*arr)[kWT], unsigned off) -> float4& {
@@ -136,8 +137,8 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
 #pragma unroll
       for (int o = 0; o < 6; ++o) {
         const unsigned col = (unsigned)((x0 + kWW - 3 + o) % nx);
-        C[o] = __ldg(cin + row + col);
-        lf_split(C[o], __ldg(ux + row + col) * ia, P[o], M[o]);
+        C[o] = LD::s(cin + row + col);
+        lf_split(C[o], LD::s(ux + row + col) * ia, P[o], M[o]);
       }
       e = face_flux_x(P[0], P[1], P[2], P[3], P[4], M[5], M[4], M[3], M[2], M[1], alpha, kappa, C[2], C[3]);
     }
@@ -157,7 +158,7 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
   stage_x(kb & 1);
   fetch_x(kb + 1);  // kb + 1 <= y0 < ny
   float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (STAGE > 1) cn = ldg4(a.c + (unsigned)kb * (unsigned)nx + X);
+  if (STAGE > 1) cn = LD::v4(a.c + (unsigned)kb * (unsigned)nx + X);
   float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
   double dep = 0.0;  // stage 3, floor row: this thread's Vs-free deposit term
   __syncthreads();
@@ -251,7 +252,7 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
         if (STAGE == 3) {
           report_status(a.status, !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3])));
           if (k == 0) {  // RK3 b-weights of the floor flux: c^n/6 + c1/6 + 2 c2/3
-            const float4 c1 = ldg4(a.c1 + X);
+            const float4 c1 = LD::v4(a.c1 + X);
             const float c1v[4] = {c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -261,7 +262,7 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
       }
     }
     carry = make_float4(fup[0], fup[1], fup[2], fup[3]);
-    if (STAGE > 1 && k + 1 < y1) cn = ldg4(a.c + (unsigned)(k + 1) * (unsigned)nx + X);
+    if (STAGE > 1 && k + 1 < y1) cn = LD::v4(a.c + (unsigned)(k + 1) * (unsigned)nx + X);
   }
 
   // stage 3: the CTAs holding the floor row fold the deposit of this step (FP64, fixed
@@ -292,20 +293,31 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(kWT) rk_stage2d_wide_kernel(Args<float> a, Stage2dParams sp) {
+__global__ void __launch_bounds__(kWT, kWminB) rk_stage2d_wide_kernel(Args<float> a, Stage2dParams sp) {
   stage2d_wide_body<STAGE>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
-// Rows per segment of the four-column kernel: the longest of the candidates that still
-// gives every SM `per_sm` CTAs (the CTAs one SM holds at once), capped at kWmaxH.
+// Rows per segment of the four-column kernel.  The CTAs of a launch run in waves of
+// sm_count x per_sm (the CTAs the SMs hold at once), and a CTA's time grows with its rows
+// plus about two rows of set-up (ring fill, priming row), so take the height that
+// minimises waves x (H + 2); ties go to the fuller last wave.  Capped at kWmaxH.
 inline int stage2d_wide_rows(int nx, int ny, int sm_count, int per_sm, int override_rows) {
   if (override_rows > 0) return min(min(override_rows, ny), kWmaxH);
   const long long strips = (nx + kWW - 1) / kWW;
-  const int cand[] = {32, 24, 20, 16, 12, 8, 6, 4, 3, 2};
-  for (int H : cand) {
-    if (strips * ((ny + H - 1) / H) >= (long long)per_sm * sm_count) return min(H, ny);
+  const long long slots = (long long)max(1, per_sm) * max(1, sm_count);
+  int best = min(2, ny);
+  double best_cost = 1e300;
+  for (int H = 2; H <= kWmaxH; ++H) {
+    const long long ctas = strips * ((ny + H - 1) / H);
+    const long long waves = (ctas + slots - 1) / slots;
+    const double cost = (double)waves * (H + 2) - 1e-6 * (double)ctas / (double)(waves * slots);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = H;
+    }
+    if (H >= ny) break;
   }
-  return min(2, ny);
+  return min(best, ny);
 }
 
 template <int STAGE>

@@ -43,8 +43,10 @@ def test_variant_and_class_workloads():
 
 def test_traffic_is_reported_only_for_unchanged_sources(monkeypatch):
     name = "lbm_collide_stream"
-    nbytes, files, sha = bench.NCU_TRAFFIC[name]
-    assert bench.kernel_traffic(name) == nbytes  # captured on the committed sources
+    nbytes, files, _ = bench.NCU_TRAFFIC[name]
+    sha = bench.source_hash(files)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, name, (nbytes, files, sha))
+    assert bench.kernel_traffic(name) == nbytes  # a capture taken on the current sources
     monkeypatch.setitem(bench.NCU_TRAFFIC, name, (nbytes, files, "0" * 12))
     assert bench.kernel_traffic(name) is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, name, (nbytes, ("no_such_file.cuh",), sha))

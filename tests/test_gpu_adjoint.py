@@ -12,9 +12,10 @@ adjoint (reverse sweep with checkpoint-and-recompute) is exact up to rounding, s
     1e-10, FP32 to 1e-3;
   * FP32 against the FP64 adjoint: relative L2 <= 1e-3;
   * the checkpoint spacing does not change the result (bitwise, FP64 and FP32); autograd
-    wraps the same numbers.
+    wraps the same numbers;
+  * the 512 x 1024 FP32 gradient over 2000 steps (checkpoint every 100) against central
+    differences of the FP64 forward on 32 random unit directions, 1e-4 relative each.
 """
-import os
 
 import numpy as np
 import pytest
@@ -205,14 +206,15 @@ def test_adjoint_rejects_unsupported_and_restores_state():
 
 
 # ---- the 512 x 1024 FP32 gradient over 2000 steps (state kept every 100) -------------
-# Expected values: central differences of the FP64 forward along random unit directions
+# Expected values: central differences of the FP64 forward along 32 random unit directions
 # d (seed 1), J(c0 + 1e-3 d) - J(c0 - 1e-3 d) over 2e-3, i.e. about 1.4e-6 per node
 # (WENO5's eps = 1e-6 makes J strongly nonlinear for c near 0: a per-node step of 1e-5
 # already leaves a 1e-3 relative truncation error), and in Vs with step 1e-7.  Bound: 1e-4
-# relative, with a floor of 1e-6 sum|g d| for directions whose derivative nearly cancels.
-# Measured: FP32 adjoint within 3e-5 relative of these, dJ/dVs within 4e-7.
+# relative to each direction's difference quotient, no absolute floor.  Measured: the FP32
+# gradient within 2e-6 .. 7.7e-5 of the quotients (median 2.4e-5; the FP64 gradient within
+# 5e-6), dJ/dVs within 4e-7.
 
-def _full_fd_check(n_dirs):
+def test_adjoint_512x1024_2000_steps_fd_32_directions():
     from paper_2106_07694_gb300 import lbm_wenoc as lw
     from paper_2106_07694_gb300 import workloads
     wl = workloads.ADJOINT_2D
@@ -233,24 +235,18 @@ def _full_fd_check(n_dirs):
     assert J == pytest.approx(J64(c0), rel=1e-5, abs=1e-9)
     rng = np.random.default_rng(1)
     h = 1e-3
-    for _ in range(n_dirs):
+    worst = 0.0
+    for i in range(32):
         d = rng.standard_normal(c0.shape)
         d /= np.linalg.norm(d)
         fd = (J64(c0 + h * d) - J64(c0 - h * d)) / (2 * h)
         got = float(np.sum(g * d))
-        assert abs(got - fd) <= 1e-4 * abs(fd) + 1e-6 * float(np.sum(np.abs(g * d))), (got, fd)
+        rel = abs(got - fd) / abs(fd)
+        worst = max(worst, rel)
+        assert rel <= 1e-4, (i, got, fd, rel)
+    print(f"worst |g.d - fd| / |fd| over 32 directions: {worst:.3g}")
     hv = 1e-7
     sp = lw.Simulation(wl.shape, fp64=True, settling_velocity=vs + hv, **kw)
     sm = lw.Simulation(wl.shape, fp64=True, settling_velocity=vs - hv, **kw)
     fdv = (J64(c0, sp) - J64(c0, sm)) / (2 * hv)
     assert dvs == pytest.approx(fdv, rel=1e-5)
-
-
-def test_adjoint_512x1024_2000_steps_fd_8_directions():
-    _full_fd_check(8)
-
-
-@pytest.mark.slow
-@pytest.mark.skipif(os.environ.get("LW_RUN_SLOW") != "1", reason="32 directions take ~5 min; LW_RUN_SLOW=1")
-def test_adjoint_512x1024_2000_steps_fd_32_directions():
-    _full_fd_check(32)
