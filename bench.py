@@ -463,8 +463,9 @@ def bench_ours(args):
 
 def bench_batch(args):
     """64 independent 2D instances (sizes and parameters of workloads.batch_sweep) advanced
-    by one launch per kernel type and step, against the same instances run one after the
-    other on the same GPU (each for the same number of steps)."""
+    by the persistent launch (per-size segment heights from the autotuner), against the same
+    batch with one launch per kernel type and step, and against the instances run one after
+    the other on the same GPU (each for the same number of steps)."""
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     from paper_2106_07694_gb300 import build as lbuild
@@ -490,10 +491,20 @@ def bench_batch(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     launches = lw.lbm_wenoc_batch_launch_count(b.handle) - l0
-    for inst in b.instances:
-        if inst.status() != lw.LW_OK:
-            raise RuntimeError("device status set in the batched run")
+    if b.status() != lw.LW_OK:
+        raise RuntimeError("device status set in the batched run")
     value = nodes * args.steps / (ms * 1e-3) / 1e9
+    # the same batch with one launch per kernel type and step instead of the persistent launch
+    b.set_persistent(False)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0.record()
+    b.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    grouped_ms = e0.elapsed_time(e1)
+    if b.status() != lw.LW_OK:
+        raise RuntimeError("device status set in the grouped batched run")
     b.close()
     # sequential: the same instances one after the other, same number of steps each
     seq_ms = 0.0
@@ -518,6 +529,9 @@ def bench_batch(args):
                    "autotuned_segment_rows": rows, "seed": 0},
         "sequential": {"value": seq, "unit": UNIT, "ms_per_step": seq_ms / args.steps,
                        "note": "each instance alone through lbm_wenoc_step, one after the other"},
+        "grouped": {"value": nodes * args.steps / (grouped_ms * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": grouped_ms / args.steps,
+                    "note": "same batch, one launch per kernel type and step instead of the persistent launch"},
         "batched_over_sequential": value / seq,
         "step_roofline": {"bound": "hbm", "alg_bytes_per_node": 80, "achieved": 80 * value, "peak": peak,
                           "unit": "GB/s", "frac": 80 * value / peak},

@@ -174,12 +174,17 @@ int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows);
 
 /* ---- Batched simulations (the paper's parameter sweep, Sec. 2.2 Table 1, as one job) ----
  * count independent 2D FP32 simulations with walls (no LW_FP64, LW_PERIODIC_VERTICAL,
- * LW_FROZEN_VELOCITY or LW_FUSED_RK3), each with its own size and parameters, in one
- * caller-owned workspace, advanced together by one launch per kernel type and step. */
+ * LW_FROZEN_VELOCITY, LW_FUSED_RK3, LW_SUGAR, scheme variants, classes or LW_ONE_COLUMN),
+ * each with its own size and parameters, in one caller-owned workspace.  By default they
+ * advance together in one persistent cooperative launch per graph of up to 16 steps: as
+ * many CTAs as the SMs hold at once take (instance, tile) work items of each phase of a
+ * step (fluid part, three RK3 stages), with a grid barrier between phases whose waits are
+ * bounded (a wait past the limit ends the launch and the batch status reads LW_ETIMEOUT).
+ * Results are bitwise those of each instance stepped alone, the deposits included. */
 typedef struct lbm_wenoc_batch lbm_wenoc_batch;
 
 /* Workspace bytes for count instances with parameters p[0..count); LW_EINVAL if any
- * instance is not a 2D FP32 walled configuration. */
+ * instance is not a 2D FP32 walled configuration of the default scheme. */
 int lbm_wenoc_batch_workspace_bytes(const lbm_wenoc_params* p, int32_t count, size_t* bytes);
 
 /* Create the batch over dev_workspace (256-byte aligned, at least the bytes above). */
@@ -195,9 +200,29 @@ lbm_wenoc* lbm_wenoc_batch_instance(lbm_wenoc_batch* b, int32_t i);
  * initialised and at the same step count, else LW_ESTATE. */
 int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps);
 
-/* Autotuner: times steps_per_trial batched steps for each candidate segment height of
- * the transport kernels (8, 16, 32, 64 rows) on a trial state, keeps the fastest and
- * returns it in *chosen_rows.  Leaves every instance uninitialised: call it before init. */
+/* persistent = 1: the persistent launch (default where the device supports cooperative
+ * launches; else LW_EINVAL); 0: one launch per kernel type and step.  Same results.
+ * Synchronises the stream; drops captured graphs. */
+int lbm_wenoc_batch_set_persistent(lbm_wenoc_batch* b, int32_t persistent);
+
+/* Bound of a grid-barrier wait of the persistent launch, in SM clock cycles (default
+ * 2^31, about one second).  skip_cta >= 0 is for testing the timeout path: that CTA of the
+ * next launch leaves before its first barrier, so the others' waits run out and the
+ * batch status becomes LW_ETIMEOUT (the instances' fields are then undefined until
+ * re-initialised).  -1: none.  Synchronises the stream. */
+int lbm_wenoc_batch_set_wait_limit(lbm_wenoc_batch* b, int64_t cycles, int32_t skip_cta);
+
+/* Synchronise; LW_ETIMEOUT if a barrier wait of a persistent launch gave up (launches
+ * after that one do nothing until this call has reported it; it clears the flag, and the
+ * instances must be initialised again), else the first non-OK instance status
+ * (LW_EUNSTABLE), else LW_OK. */
+int lbm_wenoc_batch_status(lbm_wenoc_batch* b);
+
+/* Autotuner of the segment heights: starting from each instance's default, tries the
+ * heights 4 .. 64 for each lattice size in turn (instances of one size share one), timing
+ * steps_per_trial batched steps of the whole batch on a trial state, and keeps what is
+ * fastest.  chosen_rows: NULL or count int32 slots for each instance's height.  Leaves every
+ * instance uninitialised: call it before init. */
 int lbm_wenoc_batch_autotune(lbm_wenoc_batch* b, int32_t steps_per_trial, int32_t* chosen_rows);
 
 /* Kernel launches issued by lbm_wenoc_batch_step so far. */

@@ -1,12 +1,23 @@
-// Batched launches: many independent 2D FP32 simulations of different sizes and
-// parameters advanced by one launch per kernel type (the paper's parameter sweep over
-// initial concentration and particle diameter, Sec. 2.2 Table 1, run as one job).
+// Batched simulations: many independent 2D FP32 simulations of different sizes and
+// parameters advanced together (the paper's parameter sweep over initial concentration
+// and particle diameter, Sec. 2.2 Table 1, run as one job).
 //
-// Each launch covers the blocks of every instance back to back.  Block b finds its
-// instance i by a binary search in the prefix table start[] (start[i] = first block of
-// instance i), copies that instance's argument block into shared memory and runs the
-// same body as the single-instance kernel on its local block coordinates.  The deposit
-// of each instance is folded by that instance's floor CTAs with its own ticket.
+// Persistent form (default): one cooperative launch of as many CTAs as the SMs hold at
+// once advances every instance by up to kPersistSteps steps.  A step is four phases --
+// the fluid part (collide-stream), then the three RK3 stages of the transport -- over a
+// work list of (instance, tile) items; a grid barrier separates the phases.  Fluid items
+// are one row by 256 columns, dealt round-robin (uniform cost); stage items are one
+// four-column-kernel strip by one row segment (the segment height is the instance's own,
+// chosen by the autotuner), taken from a per-phase counter so that uneven items balance.
+// The barrier waits on a generation word with a clock64 bound: a CTA that waits longer
+// than the limit sets kStatusTimeout in the batch status word and returns, and every
+// other CTA leaves at its next wait, so the launch ends and the host reads LW_ETIMEOUT.
+// Every field the launch writes is read back at L2 (LoadL2): L1 is not coherent between
+// SMs within a launch.
+//
+// Grouped form: one launch per kernel type and step; block b finds its instance by a
+// binary search in the prefix table of block counts and runs the single-instance body.
+// Both forms run the same per-node arithmetic as the single-instance kernels.
 #pragma once
 #include "common.cuh"
 #include "lbm_kernels.cuh"
@@ -14,14 +25,24 @@
 
 namespace lw {
 
+constexpr int kPersistSteps = 16;  // steps per persistent launch (work counters per launch)
+constexpr int kFluidCols = 256;    // columns of a fluid item (64 threads x 4 nodes)
+constexpr int kFluidInFlight = 2;  // nodes per thread whose populations are loaded together
+constexpr int kPersistMinB = 8;    // CTAs per SM the persistent kernel's registers must allow
+
 struct BatchTables {
   const Args<float>* args;  // [count]
-  const int* lbm_start;     // [count + 1] prefix of fluid-kernel blocks
-  const int* lbm_gx;        // [count] fluid blocks per row
-  const int* st_start;      // [count + 1] prefix of stage-kernel blocks
+  const int* lbm_start;     // [count + 1] prefix of fluid-kernel blocks (grouped form)
+  const int* lbm_gx;        // [count] fluid blocks per row (grouped form)
+  const int* st_start;      // [count + 1] prefix of stage items / blocks
   const int* st_strips;     // [count] strips per instance
   const int* st_rows;       // [count] rows per segment
+  const int* fl_start;      // [count + 1] prefix of fluid items (persistent form)
+  const int* fl_chunks;     // [count] 256-column chunks per row
   int count;
+  unsigned* bar;     // [0] arrivals at the current barrier, [1] generation (zeroed per launch)
+  unsigned* status;  // [0] batch status (kStatusTimeout)
+  unsigned* queue;   // stage-item counters, 3 per step (zeroed per launch)
 };
 
 __device__ __forceinline__ int find_instance(const int* start, int count, int b) {
@@ -35,6 +56,8 @@ __device__ __forceinline__ int find_instance(const int* start, int count, int b)
   }
   return lo;
 }
+
+// ------------------------------------------------------------------ grouped form
 
 template <int PARITY>
 __global__ void __launch_bounds__(128) lbm_d2q9_batch_kernel(BatchTables t) {
@@ -54,6 +77,7 @@ __global__ void __launch_bounds__(128) lbm_d2q9_batch_kernel(BatchTables t) {
 
 template <int STAGE>
 __global__ void __launch_bounds__(kWT) stage2d_batch_kernel(BatchTables t) {
+  __shared__ __align__(16) StageWideSmem S;
   __shared__ Args<float> sa;
   __shared__ int s_meta[4];
   if (threadIdx.x == 0) {
@@ -71,7 +95,148 @@ __global__ void __launch_bounds__(kWT) stage2d_batch_kernel(BatchTables t) {
   sp.cin = STAGE == 1 ? sa.c : (STAGE == 2 ? sa.c1 : sa.c2);
   sp.cout = STAGE == 1 ? sa.c1 : (STAGE == 2 ? sa.c2 : sa.c);
   sp.H = s_meta[3];
-  stage2d_wide_body<STAGE>(sa, sp, s_meta[0], s_meta[1], s_meta[2]);
+  stage2d_wide_body<STAGE>(S, sa, sp, s_meta[0], s_meta[1], s_meta[2]);
+}
+
+// ------------------------------------------------------------------ persistent form
+
+// Grid barrier with a bounded wait.  Returns false (and leaves kStatusTimeout set) when
+// this CTA gave up or another one already had.
+__device__ __forceinline__ bool batch_grid_sync(const BatchTables& t, unsigned nblocks, long long limit,
+                                                int& s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = t.bar + 1;
+    volatile unsigned* st = t.status;
+    const unsigned g0 = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(t.bar, 1u) + 1u == nblocks) {
+      t.bar[0] = 0u;  // only this CTA touches the count until the generation moves
+      __threadfence();
+      atomicAdd(t.bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (*st & kStatusTimeout) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > limit) {
+          atomicOr(t.status, kStatusTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Fluid phase of every instance: item = one row by 256 columns, 64 threads x 4 nodes
+// (x = x0 + t + 64 q: coalesced), round-robin over the CTAs.
+template <int PARITY>
+__device__ __forceinline__ void batch_fluid_phase(const BatchTables& t, Args<float>& sa, int& s_inst) {
+  const int total = __ldg(t.fl_start + t.count);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = find_instance(t.fl_start, t.count, item);
+    if (i != s_inst) {  // uniform: s_inst changes only between the two barriers below
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sa = t.args[i];
+        s_inst = i;
+      }
+      __syncthreads();
+    }
+    const int local = item - __ldg(t.fl_start + i);
+    const int chunks = __ldg(t.fl_chunks + i);
+    const int y = local / chunks, x0 = (local % chunks) * kFluidCols;
+#pragma unroll 1
+    for (int q0 = 0; q0 < 4; q0 += kFluidInFlight) {  // kFluidInFlight nodes' loads in flight at a time
+      float g[kFluidInFlight][9];
+      D2Q9Node nd[kFluidInFlight];
+#pragma unroll
+      for (int q = 0; q < kFluidInFlight; ++q) {
+        const int x = x0 + (int)threadIdx.x + 64 * (q0 + q);
+        nd[q] = d2q9_node(sa, x < sa.nx ? x : 0, y);
+        if (x < sa.nx) d2q9_load<float, PARITY, LoadL2>(sa, nd[q], g[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kFluidInFlight; ++q) {
+        if (x0 + (int)threadIdx.x + 64 * (q0 + q) < sa.nx)
+          d2q9_collide_store<float, PARITY, false, false, LoadL2>(sa, nd[q], g[q], nullptr);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One RK3 stage of every instance: items taken from the phase's counter.
+template <int STAGE>
+__device__ __forceinline__ void batch_stage_phase(const BatchTables& t, unsigned* counter, StageWideSmem& S,
+                                                  Args<float>& sa, int& s_inst, int* s_meta) {
+  const int total = __ldg(t.st_start + t.count);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int item = (int)atomicAdd(counter, 1u);
+      s_meta[0] = item;
+      if (item < total) {
+        const int i = find_instance(t.st_start, t.count, item);
+        if (i != s_inst) {
+          sa = t.args[i];
+          s_inst = i;
+        }
+        const int local = item - __ldg(t.st_start + i);
+        const int strips = __ldg(t.st_strips + i);
+        s_meta[1] = local % strips;
+        s_meta[2] = local / strips;
+        s_meta[3] = strips;
+        s_meta[4] = __ldg(t.st_rows + i);
+      }
+    }
+    __syncthreads();
+    if (s_meta[0] >= total) break;
+    Stage2dParams sp;
+    sp.cin = STAGE == 1 ? sa.c : (STAGE == 2 ? sa.c1 : sa.c2);
+    sp.cout = STAGE == 1 ? sa.c1 : (STAGE == 2 ? sa.c2 : sa.c);
+    sp.H = s_meta[4];
+    stage2d_wide_body<STAGE, LoadL2>(S, sa, sp, s_meta[1], s_meta[2], s_meta[3]);
+    __syncthreads();
+  }
+  __syncthreads();
+}
+
+// nsteps (<= kPersistSteps) coupled steps of every instance from AA parity `parity`.
+// skip_cta >= 0: that CTA leaves before its first barrier (a host-made fault that the
+// bounded wait turns into LW_ETIMEOUT).
+__global__ void __launch_bounds__(kWT, kPersistMinB) batch_persistent_kernel(BatchTables t, int parity, int nsteps,
+                                                               long long wait_limit, int skip_cta) {
+  __shared__ __align__(16) StageWideSmem S;
+  __shared__ Args<float> sa;
+  __shared__ int s_inst, s_ok;
+  __shared__ int s_meta[5];
+  // a launch after a timeout that has not been read yet does nothing (the state is undefined)
+  if ((int)blockIdx.x == skip_cta || (*reinterpret_cast<volatile unsigned*>(t.status) & kStatusTimeout)) return;
+  if (threadIdx.x == 0) s_inst = -1;
+  __syncthreads();
+  const unsigned nb = gridDim.x;
+  for (int k = 0; k < nsteps; ++k) {
+    if (((parity + k) & 1) == 0)
+      batch_fluid_phase<0>(t, sa, s_inst);
+    else
+      batch_fluid_phase<1>(t, sa, s_inst);
+    if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
+    batch_stage_phase<1>(t, t.queue + 3 * k, S, sa, s_inst, s_meta);
+    if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
+    batch_stage_phase<2>(t, t.queue + 3 * k + 1, S, sa, s_inst, s_meta);
+    if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
+    batch_stage_phase<3>(t, t.queue + 3 * k + 2, S, sa, s_inst, s_meta);
+    if (k + 1 < nsteps && !batch_grid_sync(t, nb, wait_limit, s_ok)) return;
+  }
 }
 
 }  // namespace lw

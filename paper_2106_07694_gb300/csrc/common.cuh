@@ -43,14 +43,20 @@ struct Args {
 };
 
 // Global-load policies.  LoadNC reads through the non-coherent (read-only) path, for data
-// no thread writes while the kernel runs; LoadCoherent issues plain loads, for kernels
-// that read what other CTAs wrote earlier in the same launch (after a grid barrier).
+// no thread writes while the kernel runs; LoadL2 reads at L2 (ld.global.cg: no L1 line is
+// kept), for a kernel that reads what other CTAs wrote earlier in the same launch, after
+// a grid barrier; LoadPlain is an ordinary load.
 struct LoadNC {
   static __device__ __forceinline__ float s(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ double s(const double* p) { return __ldg(p); }
   static __device__ __forceinline__ float4 v4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 };
-struct LoadCoherent {
+struct LoadL2 {
+  static __device__ __forceinline__ float s(const float* p) { return __ldcg(p); }
+  static __device__ __forceinline__ double s(const double* p) { return __ldcg(p); }
+  static __device__ __forceinline__ float4 v4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+};
+struct LoadPlain {
   static __device__ __forceinline__ float s(const float* p) { return *p; }
   static __device__ __forceinline__ double s(const double* p) { return *p; }
   static __device__ __forceinline__ float4 v4(const float* p) { return *reinterpret_cast<const float4*>(p); }

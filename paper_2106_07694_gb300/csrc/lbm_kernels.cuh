@@ -211,8 +211,9 @@ __device__ __forceinline__ void d2q9_load(const Args<T>& a, const D2Q9Node& nd, 
   }
 }
 
-// Moments, BGK-Guo collision and the in-place AA store of one node.
-template <typename T, int PARITY, bool RHO, bool SUGAR>
+// Moments, BGK-Guo collision and the in-place AA store of one node (LD: how c and S are
+// read, see common.cuh).
+template <typename T, int PARITY, bool RHO, bool SUGAR, class LD = LoadPlain>
 __device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9Node& nd, const T (&g)[9],
                                                    T* rho_out) {
   const unsigned n = (unsigned)a.n;
@@ -225,9 +226,9 @@ __device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9N
     if (D2Q9::cx(i)) jx += D2Q9::cx(i) * g[i];
     if (D2Q9::cy(i)) jy += D2Q9::cy(i) * g[i];
   }
-  const T cn = a.c[node];
+  const T cn = LD::s(a.c + node);
   T Fy = a.bf[1] - a.A * cn;
-  if (SUGAR) Fy -= a.gS * a.S[node] * (T(1) - a.phi0 * cn);
+  if (SUGAR) Fy -= a.gS * LD::s(a.S + node) * (T(1) - a.phi0 * cn);
   const T Fx = a.bf[0];
   const T rho = T(1) + drho;
   const T inv_rho = T(1) / rho;

@@ -907,14 +907,18 @@ void lbm_wenoc_destroy(lbm_wenoc* h) {
 struct lbm_wenoc_batch {
   std::vector<lbm_wenoc*> inst;
   std::vector<size_t> offsets;  // workspace offset of each instance
+  std::vector<int> rows;        // segment rows of each instance's stage items
   unsigned char* ws = nullptr;
   size_t tables_off = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
-  int rows = 0;  // segment rows of the stage kernels (0: per-instance default)
   int lbm_blocks = 0, st_blocks = 0;
   lw::BatchTables tab{};
-  static constexpr int kGraphSteps = 16;
+  bool persistent = true;        // one cooperative launch per graph of steps, else grouped launches
+  int grid = 0;                  // CTAs of the persistent launch (all resident at once)
+  int64_t wait_limit = 1LL << 31;  // clock64 cycles a barrier wait may take (about 1 s)
+  int skip_cta = -1;             // testing: this CTA leaves the next launch before its first barrier
+  static constexpr int kGraphSteps = lw::kPersistSteps;
   cudaGraphExec_t graph_many[2] = {nullptr, nullptr};
   cudaGraphExec_t graph_one[2] = {nullptr, nullptr};
   int64_t launches = 0;
@@ -924,13 +928,16 @@ namespace {
 
 bool batch_params_ok(const lbm_wenoc_params& p) {
   return check_params(&p) == LW_OK && p.dim == 2 && !(p.flags & LW_FP64) && !(p.flags & LW_PERIODIC_VERTICAL) &&
-         !(p.flags & (LW_FROZEN_VELOCITY | LW_FUSED_RK3 | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT)) && p.n_classes < 2 &&
-         (p.nx + lw::kWW - 1) / lw::kWW <= lw::kMaxReduceBlocks;
+         !(p.flags & (LW_FROZEN_VELOCITY | LW_FUSED_RK3 | LW_SUGAR | LW_WENO3 | LW_SIGN_SPLIT | LW_ONE_COLUMN)) &&
+         p.n_classes < 2 && (p.nx + lw::kWW - 1) / lw::kWW <= lw::kMaxReduceBlocks;
 }
 
+// Tables: the argument blocks, eight int tables, the barrier, status and work-counter words.
+constexpr int kBatchSyncWords = 8 + 3 * lw::kPersistSteps;  // bar[2], status[2], pad, queue
+
 size_t batch_tables_bytes(int count) {
-  return align_up(sizeof(Args<float>) * count, 256) + align_up(sizeof(int) * (count + 1), 256) * 2 +
-         align_up(sizeof(int) * count, 256) * 3;
+  return align_up(sizeof(Args<float>) * count, 256) + align_up(sizeof(int) * (count + 1), 256) * 3 +
+         align_up(sizeof(int) * count, 256) * 4 + align_up(sizeof(unsigned) * kBatchSyncWords, 256);
 }
 
 void batch_destroy_graphs(lbm_wenoc_batch* b) {
@@ -945,54 +952,87 @@ void batch_destroy_graphs(lbm_wenoc_batch* b) {
 int batch_upload_tables(lbm_wenoc_batch* b) {
   const int count = (int)b->inst.size();
   std::vector<Args<float>> args(count);
-  std::vector<int> lstart(count + 1), lgx(count), sstart(count + 1), sstrips(count), srows(count);
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || sms <= 0) sms = 148;
-  lstart[0] = sstart[0] = 0;
+  std::vector<int> lstart(count + 1), lgx(count), sstart(count + 1), sstrips(count), srows(count), fstart(count + 1),
+      fchunks(count);
+  lstart[0] = sstart[0] = fstart[0] = 0;
   for (int i = 0; i < count; ++i) {
     lbm_wenoc* h = b->inst[i];
     args[i] = make_args<float>(h);
     lgx[i] = (h->p.nx + kLbmThreads - 1) / kLbmThreads;
     lstart[i + 1] = lstart[i] + lgx[i] * h->p.ny;
     sstrips[i] = (h->p.nx + lw::kWW - 1) / lw::kWW;
-    srows[i] = b->rows > 0 ? std::min(std::min(b->rows, h->p.ny), lw::kWmaxH) : h->stage2d_rows;
+    srows[i] = std::min(std::min(b->rows[i] > 0 ? b->rows[i] : h->stage2d_rows, h->p.ny), lw::kWmaxH);
     const int segs = (h->p.ny + srows[i] - 1) / srows[i];
     sstart[i + 1] = sstart[i] + sstrips[i] * segs;
+    fchunks[i] = (h->p.nx + lw::kFluidCols - 1) / lw::kFluidCols;
+    fstart[i + 1] = fstart[i] + fchunks[i] * h->p.ny;
   }
   b->lbm_blocks = lstart[count];
   b->st_blocks = sstart[count];
   unsigned char* base = b->ws + b->tables_off;
   size_t off = 0;
-  auto put = [&](const void* src, size_t nbytes) -> const void* {
+  auto put = [&](const void* src, size_t nbytes) -> void* {
     unsigned char* dst = base + off;
     off += align_up(nbytes, 256);
-    if (cudaMemcpyAsync(dst, src, nbytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) return nullptr;
+    if (src && cudaMemcpyAsync(dst, src, nbytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) return nullptr;
     return dst;
   };
   b->tab.args = static_cast<const Args<float>*>(put(args.data(), sizeof(Args<float>) * count));
   b->tab.lbm_start = static_cast<const int*>(put(lstart.data(), sizeof(int) * (count + 1)));
   b->tab.st_start = static_cast<const int*>(put(sstart.data(), sizeof(int) * (count + 1)));
+  b->tab.fl_start = static_cast<const int*>(put(fstart.data(), sizeof(int) * (count + 1)));
   b->tab.lbm_gx = static_cast<const int*>(put(lgx.data(), sizeof(int) * count));
   b->tab.st_strips = static_cast<const int*>(put(sstrips.data(), sizeof(int) * count));
   b->tab.st_rows = static_cast<const int*>(put(srows.data(), sizeof(int) * count));
+  b->tab.fl_chunks = static_cast<const int*>(put(fchunks.data(), sizeof(int) * count));
+  unsigned* sync = static_cast<unsigned*>(put(nullptr, sizeof(unsigned) * kBatchSyncWords));
+  b->tab.bar = sync;
+  b->tab.status = sync + 2;
+  b->tab.queue = sync + 8;
   b->tab.count = count;
-  if (!b->tab.args || !b->tab.lbm_start || !b->tab.st_start || !b->tab.lbm_gx || !b->tab.st_strips || !b->tab.st_rows)
+  if (!b->tab.args || !b->tab.lbm_start || !b->tab.st_start || !b->tab.fl_start || !b->tab.lbm_gx ||
+      !b->tab.st_strips || !b->tab.st_rows || !b->tab.fl_chunks)
     return LW_ECUDA;
+  if (cudaMemsetAsync(sync, 0, sizeof(unsigned) * kBatchSyncWords, b->stream) != cudaSuccess) return LW_ECUDA;
   // the host vectors go out of scope: wait for the copies
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LW_ECUDA;
   batch_destroy_graphs(b);
   return LW_OK;
 }
 
-void batch_enqueue(lbm_wenoc_batch* b, cudaStream_t s, int parity) {
+// `count` steps from AA parity `parity`: one persistent launch (count <= kPersistSteps), or
+// four grouped launches per step.
+cudaError_t batch_enqueue(lbm_wenoc_batch* b, cudaStream_t s, int parity, int count) {
   const lw::BatchTables t = b->tab;
-  if (parity == 0)
-    lw::lbm_d2q9_batch_kernel<0><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
-  else
-    lw::lbm_d2q9_batch_kernel<1><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
-  lw::stage2d_batch_kernel<1><<<b->st_blocks, lw::kWT, 0, s>>>(t);
-  lw::stage2d_batch_kernel<2><<<b->st_blocks, lw::kWT, 0, s>>>(t);
-  lw::stage2d_batch_kernel<3><<<b->st_blocks, lw::kWT, 0, s>>>(t);
+  if (b->persistent) {
+    // the barrier words and the work counters start at zero; the status word is kept
+    cudaError_t e = cudaMemsetAsync(t.bar, 0, sizeof(unsigned) * 2, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t.queue, 0, sizeof(unsigned) * 3 * lw::kPersistSteps, s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(lw::kWT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const long long limit = (long long)b->wait_limit;
+    return cudaLaunchKernelEx(&cfg, lw::batch_persistent_kernel, t, parity, count, limit, b->skip_cta);
+  }
+  for (int k = 0; k < count; ++k) {
+    const int par = (parity + k) & 1;
+    if (par == 0)
+      lw::lbm_d2q9_batch_kernel<0><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
+    else
+      lw::lbm_d2q9_batch_kernel<1><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
+    lw::stage2d_batch_kernel<1><<<b->st_blocks, lw::kWT, 0, s>>>(t);
+    lw::stage2d_batch_kernel<2><<<b->st_blocks, lw::kWT, 0, s>>>(t);
+    lw::stage2d_batch_kernel<3><<<b->st_blocks, lw::kWT, 0, s>>>(t);
+  }
+  return cudaGetLastError();
 }
 
 int batch_capture(lbm_wenoc_batch* b, int parity, int count, cudaGraphExec_t* out) {
@@ -1001,8 +1041,9 @@ int batch_capture(lbm_wenoc_batch* b, int parity, int count, cudaGraphExec_t* ou
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int k = 0; k < count; ++k) batch_enqueue(b, cap, (parity + k) & 1);
+    cudaError_t e2 = batch_enqueue(b, cap, parity, count);
     e = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   if (g) cudaGraphDestroy(g);
@@ -1010,7 +1051,10 @@ int batch_capture(lbm_wenoc_batch* b, int parity, int count, cudaGraphExec_t* ou
   return e == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
-// Advance every instance; requires equal step counts (shared AA parity).
+int64_t batch_launches(const lbm_wenoc_batch* b, int count) { return b->persistent ? 1 : 4LL * count; }
+
+// Advance every instance; requires equal step counts (shared AA parity).  Graphs of
+// kGraphSteps steps (and of one step for the rest) are captured once per parity.
 int batch_advance(lbm_wenoc_batch* b, int64_t nsteps, bool require_init) {
   if (nsteps < 0) return LW_EINVAL;
   const int par = b->inst[0]->parity;
@@ -1020,25 +1064,58 @@ int batch_advance(lbm_wenoc_batch* b, int64_t nsteps, bool require_init) {
   }
   int64_t left = nsteps;
   int parity = par;
+  int64_t launches = 0;
   while (left > 0) {
     const bool many = left >= lbm_wenoc_batch::kGraphSteps;
-    cudaGraphExec_t* slot = many ? &b->graph_many[parity] : &b->graph_one[parity];
     const int count = many ? lbm_wenoc_batch::kGraphSteps : 1;
-    if (!*slot) {
-      int rc = batch_capture(b, parity, count, slot);
-      if (rc != LW_OK) return rc;
+    if (b->skip_cta >= 0) {  // testing launch: not captured
+      if (batch_enqueue(b, b->stream, parity, count) != cudaSuccess) return LW_ECUDA;
+      b->skip_cta = -1;
+    } else {
+      cudaGraphExec_t* slot = many ? &b->graph_many[parity] : &b->graph_one[parity];
+      if (!*slot) {
+        int rc = batch_capture(b, parity, count, slot);
+        if (rc != LW_OK) return rc;
+      }
+      if (cudaGraphLaunch(*slot, b->stream) != cudaSuccess) return LW_ECUDA;
     }
-    if (cudaGraphLaunch(*slot, b->stream) != cudaSuccess) return LW_ECUDA;
-    b->launches += 4LL * count;
+    launches += batch_launches(b, count);
     parity = (parity + count) & 1;
     left -= count;
   }
+  b->launches += launches;
   for (lbm_wenoc* h : b->inst) {
     h->parity = parity;
     h->steps += nsteps;
     h->launches += 4 * nsteps;
   }
   return cudaGetLastError() == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+// Trial state of the autotuner: c = 0 and the fluid at rest in every instance.
+int batch_trial_state(lbm_wenoc_batch* b) {
+  for (lbm_wenoc* h : b->inst) {
+    if (cudaMemsetAsync(h->ws + h->L.c, 0, (size_t)h->n * sizeof(float), b->stream) != cudaSuccess) return LW_ECUDA;
+    if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * kScalars, b->stream) != cudaSuccess)
+      return LW_ECUDA;
+    if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, b->stream) != cudaSuccess) return LW_ECUDA;
+    h->cur = 0;
+    launch_init<D2Q9, float>(h, nullptr);
+    h->parity = 0;
+    h->steps = 0;
+  }
+  return LW_OK;
+}
+
+// Milliseconds of `steps` batched steps (after one untimed step).
+int batch_time(lbm_wenoc_batch* b, int steps, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  int rc = batch_advance(b, 1, false);
+  if (rc != LW_OK) return rc;
+  cudaEventRecord(e0, b->stream);
+  if ((rc = batch_advance(b, steps, false)) != LW_OK) return rc;
+  cudaEventRecord(e1, b->stream);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return LW_ECUDA;
+  return cudaEventElapsedTime(ms, e0, e1) == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
 }  // namespace
@@ -1070,12 +1147,24 @@ int lbm_wenoc_batch_create(const lbm_wenoc_params* p, int32_t count, void* dev_w
   b->ws = static_cast<unsigned char*>(dev_workspace);
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&b->device);
+  // every CTA of the persistent launch must be resident at once (the grid barrier waits
+  // for all of them): as many as the SMs hold
+  int sms = 0, per_sm = 0, coop = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || sms <= 0 ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lw::batch_persistent_kernel, lw::kWT, 0) !=
+          cudaSuccess) {
+    delete b;
+    return LW_ECUDA;
+  }
+  b->grid = per_sm * sms;
+  b->persistent = coop != 0 && b->grid > 0;
   size_t off = 0;
   for (int i = 0; i < count; ++i) {
     const size_t sz = align_up(make_layout(p[i]).total, 256);
     lbm_wenoc* h = nullptr;
     rc = lbm_wenoc_create(&p[i], b->ws + off, sz, cuda_stream, &h);
-    if (rc != LW_OK || !h->stage2d) {
+    if (rc != LW_OK || !h->wide) {
       if (h) lbm_wenoc_destroy(h);
       for (lbm_wenoc* q : b->inst) lbm_wenoc_destroy(q);
       delete b;
@@ -1085,6 +1174,7 @@ int lbm_wenoc_batch_create(const lbm_wenoc_params* p, int32_t count, void* dev_w
     b->offsets.push_back(off);
     off += sz;
   }
+  b->rows.assign(count, 0);
   b->tables_off = off;
   rc = batch_upload_tables(b);
   if (rc != LW_OK) {
@@ -1106,50 +1196,90 @@ int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps) {
   return batch_advance(b, nsteps, true);
 }
 
+int lbm_wenoc_batch_set_persistent(lbm_wenoc_batch* b, int32_t persistent) {
+  if (!b) return LW_EINVAL;
+  int coop = 0;
+  if (persistent && (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device) != cudaSuccess ||
+                     !coop || b->grid <= 0))
+    return LW_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LW_ECUDA;
+  b->persistent = persistent != 0;
+  batch_destroy_graphs(b);
+  return LW_OK;
+}
+
+int lbm_wenoc_batch_set_wait_limit(lbm_wenoc_batch* b, int64_t cycles, int32_t skip_cta) {
+  if (!b || cycles < 1 || skip_cta < -1 || skip_cta >= b->grid) return LW_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LW_ECUDA;
+  if (cycles != b->wait_limit) batch_destroy_graphs(b);  // the limit is a kernel argument of the graphs
+  b->wait_limit = cycles;
+  b->skip_cta = skip_cta;
+  return LW_OK;
+}
+
+int lbm_wenoc_batch_status(lbm_wenoc_batch* b) {
+  if (!b) return LW_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LW_ECUDA;
+  unsigned st = 0;
+  if (cudaMemcpy(&st, b->tab.status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return LW_ECUDA;
+  if (st & lw::kStatusTimeout) {  // reported once: the word is cleared for the next launches
+    if (cudaMemset(b->tab.status, 0, sizeof(unsigned)) != cudaSuccess) return LW_ECUDA;
+    return LW_ETIMEOUT;
+  }
+  for (lbm_wenoc* h : b->inst) {
+    const int rc = sync_and_status(h);
+    if (rc != LW_OK) return rc;
+  }
+  return LW_OK;
+}
+
 int lbm_wenoc_batch_autotune(lbm_wenoc_batch* b, int32_t steps_per_trial, int32_t* chosen_rows) {
   if (!b || steps_per_trial < 1) return LW_EINVAL;
-  // trial state: c = 0 and the fluid at rest in every instance (the caller inits afterwards)
-  for (lbm_wenoc* h : b->inst) {
-    if (cudaMemsetAsync(h->ws + h->L.c, 0, (size_t)h->n * sizeof(float), b->stream) != cudaSuccess) return LW_ECUDA;
-    if (cudaMemsetAsync(h->ws + h->L.scalars, 0, sizeof(double) * kScalars, b->stream) != cudaSuccess)
-      return LW_ECUDA;
-    if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, b->stream) != cudaSuccess) return LW_ECUDA;
-    h->cur = 0;
-    launch_init<D2Q9, float>(h, nullptr);
-    h->parity = 0;
-    h->steps = 0;
-  }
-  const int candidates[] = {8, 16, 32, 64};
+  const int count = (int)b->inst.size();
+  int rc = batch_trial_state(b);
+  if (rc != LW_OK) return rc;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LW_ECUDA;
-  int best = 0;
+  // start from each instance's own heuristic, then one pass of coordinate descent over the
+  // shape classes (instances of one lattice size share a segment height): try each
+  // candidate height for the class with the whole batch timed, keep the fastest
+  for (int i = 0; i < count; ++i) b->rows[i] = b->inst[i]->stage2d_rows;
+  std::vector<std::pair<int, int>> shapes;
+  for (lbm_wenoc* h : b->inst) {
+    const std::pair<int, int> sh(h->p.nx, h->p.ny);
+    if (std::find(shapes.begin(), shapes.end(), sh) == shapes.end()) shapes.push_back(sh);
+  }
+  const int candidates[] = {8, 12, 16, 20, 27, 32, 48, 64};
   float best_ms = 0.f;
-  int rc = LW_OK;
-  for (int rows : candidates) {
-    b->rows = rows;
-    if ((rc = batch_upload_tables(b)) != LW_OK) break;
-    if ((rc = batch_advance(b, 1, false)) != LW_OK) break;  // warm-up (graph capture)
-    cudaEventRecord(e0, b->stream);
-    if ((rc = batch_advance(b, steps_per_trial, false)) != LW_OK) break;
-    cudaEventRecord(e1, b->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      rc = LW_ECUDA;
-      break;
+  if ((rc = batch_upload_tables(b)) == LW_OK) rc = batch_time(b, steps_per_trial, e0, e1, &best_ms);
+  for (size_t c = 0; c < shapes.size() && rc == LW_OK; ++c) {
+    std::vector<int> keep = b->rows;
+    for (int H : candidates) {
+      if (H > shapes[c].second) break;
+      bool same = true;
+      for (int i = 0; i < count; ++i)
+        if (b->inst[i]->p.nx == shapes[c].first && b->inst[i]->p.ny == shapes[c].second) {
+          same = same && keep[i] == H;
+          b->rows[i] = H;
+        }
+      if (same) continue;
+      float ms = 0.f;
+      if ((rc = batch_upload_tables(b)) != LW_OK || (rc = batch_time(b, steps_per_trial, e0, e1, &ms)) != LW_OK)
+        break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        keep = b->rows;
+      }
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best == 0 || ms < best_ms) {
-      best = rows;
-      best_ms = ms;
-    }
+    b->rows = keep;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != LW_OK) return rc;
-  b->rows = best;
   rc = batch_upload_tables(b);
   for (lbm_wenoc* h : b->inst) h->initialised = false;  // trial state is not a user state
-  if (chosen_rows) *chosen_rows = best;
+  if (chosen_rows)
+    for (int i = 0; i < count; ++i) chosen_rows[i] = b->rows[i];
   return rc;
 }
 

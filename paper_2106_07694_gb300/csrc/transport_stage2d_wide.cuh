@@ -52,12 +52,11 @@ __device__ __forceinline__ void lf_split(float c, float w, float& p, float& m) {
   m = fmaf(w, h, -h);
 }
 
-// LD: the global-load policy (LoadNC for a launch of its own, LoadCoherent inside a kernel
+// LD: the global-load policy (LoadNC for a launch of its own, LoadL2 inside a kernel
 // whose earlier phases wrote the fields).
 template <int STAGE, class LD = LoadNC>
-__device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const Stage2dParams& sp, int bx, int by,
-                                                  int strips) {
-  __shared__ __align__(16) StageWideSmem S;
+__device__ __forceinline__ void stage2d_wide_body(StageWideSmem& S, const Args<float>& a, const Stage2dParams& sp,
+                                                  int bx, int by, int strips) {
   const int t = threadIdx.x;
   const int nx = a.nx, ny = a.ny;
   const int x0 = bx * kWW;
@@ -286,7 +285,8 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
       const volatile double* vp = a.partials;
       double tot = 0.0;
       for (int s = 0; s < strips; ++s) tot += vp[s];
-      a.scalars[0] += tot;
+      const double prev = *reinterpret_cast<volatile double*>(a.scalars);  // written by earlier steps
+      a.scalars[0] = prev + tot;
       *a.ticket = 0u;
     }
   }
@@ -294,7 +294,8 @@ __device__ __forceinline__ void stage2d_wide_body(const Args<float>& a, const St
 
 template <int STAGE>
 __global__ void __launch_bounds__(kWT, kWminB) rk_stage2d_wide_kernel(Args<float> a, Stage2dParams sp) {
-  stage2d_wide_body<STAGE>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
+  __shared__ __align__(16) StageWideSmem S;
+  stage2d_wide_body<STAGE>(S, a, sp, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // Rows per segment of the four-column kernel.  The CTAs of a launch run in waves of

@@ -42,7 +42,8 @@ EXPORTED = [
     "lbm_wenoc_launch_count", "lbm_wenoc_set_segment_rows", "lbm_wenoc_total_mass_noalloc",
     "lbm_wenoc_destroy", "lbm_wenoc_batch_workspace_bytes", "lbm_wenoc_batch_create",
     "lbm_wenoc_batch_instance", "lbm_wenoc_batch_step", "lbm_wenoc_batch_autotune",
-    "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy",
+    "lbm_wenoc_batch_launch_count", "lbm_wenoc_batch_destroy", "lbm_wenoc_batch_set_persistent",
+    "lbm_wenoc_batch_set_wait_limit", "lbm_wenoc_batch_status",
     "lbm_wenoc_gradient_workspace_bytes", "lbm_wenoc_deposit_gradient", "lbm_wenoc_set_sugar",
     "lbm_wenoc_sugar", "lbm_wenoc_set_class", "lbm_wenoc_class", "lbm_wenoc_class_deposit",
 ]
@@ -129,6 +130,9 @@ def load():
     L.lbm_wenoc_batch_launch_count.argtypes = [vp]
     L.lbm_wenoc_batch_launch_count.restype = i64
     L.lbm_wenoc_batch_destroy.argtypes = [vp]
+    L.lbm_wenoc_batch_set_persistent.argtypes = [vp, ctypes.c_int32]
+    L.lbm_wenoc_batch_set_wait_limit.argtypes = [vp, i64, ctypes.c_int32]
+    L.lbm_wenoc_batch_status.argtypes = [vp]
     L.lbm_wenoc_batch_destroy.restype = None
     L.lbm_wenoc_gradient_workspace_bytes.argtypes = [P, i64, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
     dp = ctypes.POINTER(ctypes.c_double)
@@ -463,10 +467,25 @@ def lbm_wenoc_batch_step(b, nsteps):
     return _check("lbm_wenoc_batch_step", load().lbm_wenoc_batch_step(b, int(nsteps)))
 
 
-def lbm_wenoc_batch_autotune(b, steps_per_trial=4):
-    rows = ctypes.c_int32(0)
-    _check("lbm_wenoc_batch_autotune", load().lbm_wenoc_batch_autotune(b, int(steps_per_trial), ctypes.byref(rows)))
-    return rows.value
+def lbm_wenoc_batch_autotune(b, count, steps_per_trial=4):
+    """Segment heights chosen for the `count` instances (a list)."""
+    rows = (ctypes.c_int32 * count)()
+    _check("lbm_wenoc_batch_autotune", load().lbm_wenoc_batch_autotune(b, int(steps_per_trial), rows))
+    return list(rows)
+
+
+def lbm_wenoc_batch_set_persistent(b, persistent=True):
+    return _check("lbm_wenoc_batch_set_persistent", load().lbm_wenoc_batch_set_persistent(b, 1 if persistent else 0))
+
+
+def lbm_wenoc_batch_set_wait_limit(b, cycles, skip_cta=-1):
+    return _check("lbm_wenoc_batch_set_wait_limit", load().lbm_wenoc_batch_set_wait_limit(b, int(cycles),
+                                                                                         int(skip_cta)))
+
+
+def lbm_wenoc_batch_status(b):
+    """LW_OK, LW_ETIMEOUT or an instance's status code (not raised)."""
+    return load().lbm_wenoc_batch_status(b)
 
 
 def lbm_wenoc_batch_launch_count(b):
@@ -516,7 +535,13 @@ class Batch:
         self.instances = [_Instance(self, i, sp["shape"]) for i, sp in enumerate(specs)]
 
     def autotune(self, steps_per_trial=4):
-        return lbm_wenoc_batch_autotune(self.handle, steps_per_trial)
+        return lbm_wenoc_batch_autotune(self.handle, len(self.instances), steps_per_trial)
+
+    def set_persistent(self, persistent=True):
+        lbm_wenoc_batch_set_persistent(self.handle, persistent)
+
+    def status(self):
+        return lbm_wenoc_batch_status(self.handle)
 
     def step(self, n=1):
         lbm_wenoc_batch_step(self.handle, n)

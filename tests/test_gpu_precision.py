@@ -85,7 +85,7 @@ def test_precision_128x256_against_the_oracle():
     o.step(wl.steps)
     e = _errors("128x256 FP64 build vs oracle", wl.steps, _gpu_state(g64, ny), _oracle_state(o, ny))
     assert e["c"] <= 1e-12 and e["deposit"] <= 1e-12 and e["total_mass"] <= 1e-13
-    assert e["mass_below_mid"] <= 1e-12 and e["rho_abs"] <= 1e-14
+    assert e["mass_below_mid"] <= 1e-12 and e["rho_abs"] <= 1e-12  # rho ~ 1: 1e-12 relative
 
     c32 = c0.astype(np.float32).astype(np.float64)
     g32 = Simulation(wl.shape, fp64=False, **kw)
