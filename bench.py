@@ -475,7 +475,7 @@ def bench_batch(args):
     specs = [dict(shape=w.shape, **phys_kwargs(w)) for w in wls]
     nodes = sum(w.nodes for w in wls)
     b = lw.Batch(specs)
-    rows = b.autotune(4)
+    rows = b.autotune(8)
     for inst, w in zip(b.instances, wls):
         inst.init(torch.from_numpy(w.initial_c().astype(np.float32)).cuda())
     b.step(args.warmup)

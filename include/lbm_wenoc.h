@@ -281,7 +281,9 @@ int lbm_wenoc_class_deposit(lbm_wenoc* h, int32_t k, double* out);
  * that every GPU loading the library keeps until exit; no cudaMalloc or cudaFree is
  * called.  The first call on each device looks up that array's address, so make it
  * before any stream capture.  All calls share the array: calls that overlap on the GPU
- * race and must be ordered by the caller. */
+ * race and must be ordered by the caller.  The looked-up address is kept for the life of
+ * the process: after cudaDeviceReset (or any teardown of the device's primary context)
+ * it is stale, and this entry point must not be used again in that process. */
 int lbm_wenoc_total_mass_noalloc(const void* c_dev, int64_t n, int32_t fp64, void* cuda_stream,
                                  double* out_dev);
 

@@ -22,12 +22,11 @@
 #include "common.cuh"
 #include "lbm_kernels.cuh"
 #include "transport_stage2d_wide.cuh"
+#include "fluid_rows.cuh"
 
 namespace lw {
 
 constexpr int kPersistSteps = 16;  // steps per persistent launch (work counters per launch)
-constexpr int kFluidCols = 256;    // columns of a fluid item (64 threads x 4 nodes)
-constexpr int kFluidInFlight = 2;  // nodes per thread whose populations are loaded together
 constexpr int kPersistMinB = 8;    // CTAs per SM the persistent kernel's registers must allow
 
 struct BatchTables {
@@ -137,41 +136,47 @@ __device__ __forceinline__ bool batch_grid_sync(const BatchTables& t, unsigned n
   return s_ok != 0;
 }
 
-// Fluid phase of every instance: item = one row by 256 columns, 64 threads x 4 nodes
-// (x = x0 + t + 64 q: coalesced), round-robin over the CTAs.
+// Fluid phase of every instance: item = one row by 256 columns (fluid_rows.cuh), dealt
+// round-robin over the CTAs, the next item's windows copied while the current one is
+// collided; the two window buffers overlay the stage phases' shared block.
+// the stage phases' block and the fluid phase's windows share one shared-memory buffer
+constexpr size_t kPersistSmem = sizeof(StageWideSmem) > sizeof(FluidStage) ? sizeof(StageWideSmem) : sizeof(FluidStage);
+
 template <int PARITY>
-__device__ __forceinline__ void batch_fluid_phase(const BatchTables& t, Args<float>& sa, int& s_inst) {
+__device__ __forceinline__ void fluid_issue(const BatchTables& t, int item, FluidStage& st, int buf) {
+  const int i = find_instance(t.fl_start, t.count, item);
+  const Args<float>* A = t.args + i;
+  const int local = item - __ldg(t.fl_start + i);
+  const int chunks = __ldg(t.fl_chunks + i);
+  fluid_issue_row<PARITY>(A->g, A->c, (unsigned)A->n, A->nx, A->ny, local / chunks, (local % chunks) * kFluidCols,
+                          st, buf);
+}
+
+template <int PARITY>
+__device__ __forceinline__ void batch_fluid_phase(const BatchTables& t, FluidStage& st, Args<float>& sa,
+                                                  int& s_inst) {
   const int total = __ldg(t.fl_start + t.count);
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  int item = blockIdx.x, buf = 0;
+  if (item < total) fluid_issue<PARITY>(t, item, st, 0);
+  cp_async_commit();
+  for (; item < total; item += gridDim.x, buf ^= 1) {
+    const int next = item + (int)gridDim.x;
+    if (next < total) fluid_issue<PARITY>(t, next, st, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this item's windows (the next item's copies may still fly)
     const int i = find_instance(t.fl_start, t.count, item);
-    if (i != s_inst) {  // uniform: s_inst changes only between the two barriers below
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        sa = t.args[i];
-        s_inst = i;
-      }
-      __syncthreads();
+    __syncthreads();  // every thread's copies have landed; sa and s_inst are free to change
+    if (threadIdx.x == 0 && i != s_inst) {
+      sa = t.args[i];
+      s_inst = i;
     }
+    __syncthreads();
     const int local = item - __ldg(t.fl_start + i);
     const int chunks = __ldg(t.fl_chunks + i);
-    const int y = local / chunks, x0 = (local % chunks) * kFluidCols;
-#pragma unroll 1
-    for (int q0 = 0; q0 < 4; q0 += kFluidInFlight) {  // kFluidInFlight nodes' loads in flight at a time
-      float g[kFluidInFlight][9];
-      D2Q9Node nd[kFluidInFlight];
-#pragma unroll
-      for (int q = 0; q < kFluidInFlight; ++q) {
-        const int x = x0 + (int)threadIdx.x + 64 * (q0 + q);
-        nd[q] = d2q9_node(sa, x < sa.nx ? x : 0, y);
-        if (x < sa.nx) d2q9_load<float, PARITY, LoadL2>(sa, nd[q], g[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < kFluidInFlight; ++q) {
-        if (x0 + (int)threadIdx.x + 64 * (q0 + q) < sa.nx)
-          d2q9_collide_store<float, PARITY, false, false, LoadL2>(sa, nd[q], g[q], nullptr);
-      }
-    }
+    fluid_compute_row<PARITY>(sa, local / chunks, (local % chunks) * kFluidCols, st, buf);
+    __syncthreads();  // buffer `buf` is refilled by the issue two items on
   }
+  cp_async_wait<0>();
   __syncthreads();
 }
 
@@ -215,7 +220,8 @@ __device__ __forceinline__ void batch_stage_phase(const BatchTables& t, unsigned
 // bounded wait turns into LW_ETIMEOUT).
 __global__ void __launch_bounds__(kWT, kPersistMinB) batch_persistent_kernel(BatchTables t, int parity, int nsteps,
                                                                long long wait_limit, int skip_cta) {
-  __shared__ __align__(16) StageWideSmem S;
+  __shared__ __align__(16) unsigned char smem_buf[kPersistSmem];
+  StageWideSmem& S = *reinterpret_cast<StageWideSmem*>(smem_buf);
   __shared__ Args<float> sa;
   __shared__ int s_inst, s_ok;
   __shared__ int s_meta[5];
@@ -225,10 +231,11 @@ __global__ void __launch_bounds__(kWT, kPersistMinB) batch_persistent_kernel(Bat
   __syncthreads();
   const unsigned nb = gridDim.x;
   for (int k = 0; k < nsteps; ++k) {
+    FluidStage& fs = *reinterpret_cast<FluidStage*>(smem_buf);
     if (((parity + k) & 1) == 0)
-      batch_fluid_phase<0>(t, sa, s_inst);
+      batch_fluid_phase<0>(t, fs, sa, s_inst);
     else
-      batch_fluid_phase<1>(t, sa, s_inst);
+      batch_fluid_phase<1>(t, fs, sa, s_inst);
     if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
     batch_stage_phase<1>(t, t.queue + 3 * k, S, sa, s_inst, s_meta);
     if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;

@@ -211,11 +211,11 @@ __device__ __forceinline__ void d2q9_load(const Args<T>& a, const D2Q9Node& nd, 
   }
 }
 
-// Moments, BGK-Guo collision and the in-place AA store of one node (LD: how c and S are
-// read, see common.cuh).
+// Moments, BGK-Guo collision and the in-place AA store of one node whose concentration
+// (the force's c) is cn (LD: how S is read, see common.cuh).
 template <typename T, int PARITY, bool RHO, bool SUGAR, class LD = LoadPlain>
-__device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9Node& nd, const T (&g)[9],
-                                                   T* rho_out) {
+__device__ __forceinline__ void d2q9_collide_store_c(const Args<T>& a, const D2Q9Node& nd, const T (&g)[9],
+                                                     T* rho_out, const T cn) {
   const unsigned n = (unsigned)a.n;
   const unsigned node = nd.node;
   T* __restrict__ G = a.g;
@@ -226,7 +226,6 @@ __device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9N
     if (D2Q9::cx(i)) jx += D2Q9::cx(i) * g[i];
     if (D2Q9::cy(i)) jy += D2Q9::cy(i) * g[i];
   }
-  const T cn = LD::s(a.c + node);
   T Fy = a.bf[1] - a.A * cn;
   if (SUGAR) Fy -= a.gS * LD::s(a.S + node) * (T(1) - a.phi0 * cn);
   const T Fx = a.bf[0];
@@ -270,6 +269,13 @@ __device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9N
     store(i, keep * g[i] + om * (even + odd) + (seven + sodd));
     store(i + 1, keep * g[i + 1] + om * (even - odd) + (seven - sodd));
   }
+}
+
+// The same with c (and S) read at the node through LD.
+template <typename T, int PARITY, bool RHO, bool SUGAR, class LD = LoadPlain>
+__device__ __forceinline__ void d2q9_collide_store(const Args<T>& a, const D2Q9Node& nd, const T (&g)[9],
+                                                   T* rho_out) {
+  d2q9_collide_store_c<T, PARITY, RHO, SUGAR, LD>(a, nd, g, rho_out, LD::s(a.c + nd.node));
 }
 
 // Body of the D2Q9 kernel for block (bx, by): nodes x = bx*128 + thread, row y = by.

@@ -22,6 +22,7 @@
 #include "transport_sweep3d.cuh"
 #include "transport_stage2d.cuh"
 #include "transport_stage2d_wide.cuh"
+#include "transport_sweep3d_wide.cuh"
 #include "batch.cuh"
 #include "adjoint.cuh"
 
@@ -135,6 +136,8 @@ struct lbm_wenoc {
   lw::SweepLaunch sweep_geom{};
   bool sweep3d = false;  // 3D FP32 with walls: tiled z-sweep stage kernels
   int sweep3d_rows = 0;
+  bool wide3d = false;   // ... with four columns per thread (default scheme, no sugar)
+  int wide3d_per_sm = 1;
   bool stage2d = false;  // 2D FP32 with walls: three row-sweep stage kernels
   int stage2d_rows = 0;
   bool wide = false;     // ... with four columns per thread (default scheme, no sugar)
@@ -369,6 +372,17 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
     launch(h, K_STAGE3, [&] { lw::launch_stage2d<3>(af, af.c2, af.c, H, s); });  // + deposit
     return;
   }
+  if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d && h->wide3d) {
+    const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
+    const int H = h->sweep3d_rows;
+    launch(h, K_STAGE1, [&] { lw::launch_sweep3d_wide<1>(af, af.c, af.c1, H, s); });
+    launch(h, K_STAGE2, [&] { lw::launch_sweep3d_wide<2>(af, af.c1, af.c2, H, s); });
+    launch(h, K_DEPOSIT, [&] {
+      lw::deposit_kernel<T><<<dep_blocks, lw::kReduceThreads, 0, s>>>(a, nfloor);
+    });
+    launch(h, K_STAGE3, [&] { lw::launch_sweep3d_wide<3>(af, af.c2, af.c, H, s); });
+    return;
+  }
   if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d) {
     const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
     const int H = h->sweep3d_rows;
@@ -403,6 +417,11 @@ void enqueue_one(lbm_wenoc* h, int parity) {
   }
 }
 
+// `count` steps from AA parity `parity`.
+void enqueue_many(lbm_wenoc* h, int parity, int64_t count) {
+  for (int64_t k = 0; k < count; ++k) enqueue_one(h, h->frozen ? 0 : (int)((parity + k) & 1));
+}
+
 void destroy_graphs(lbm_wenoc* h) {
   for (int i = 0; i < 4; ++i) {
     if (h->graph_many[i]) cudaGraphExecDestroy(h->graph_many[i]);
@@ -422,7 +441,7 @@ int capture_graph(lbm_wenoc* h, int parity, int count, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int k = 0; k < count; ++k) enqueue_one(h, (parity + k) & 1);
+    enqueue_many(h, parity, count);
     e = cudaStreamEndCapture(cap, &g);
   }
   h->stream = saved;
@@ -440,6 +459,8 @@ int launches_per_step(const lbm_wenoc* h) {
   const int per_class = (h->stage2d || h->sweep3d) ? (h->sweep3d ? 4 : 3) : 3 + (h->walls ? 1 : 0);
   return (h->frozen ? 0 : 1) + classes * per_class + sum + (h->sugar ? 1 : 0);
 }
+
+int64_t launches_for(const lbm_wenoc* h, int64_t count) { return (int64_t)launches_per_step(h) * count; }
 
 int sync_and_status(lbm_wenoc* h) {
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
@@ -564,10 +585,21 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   if (h->sweep3d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
-    h->sweep3d_rows = lw::sweep3d_rows(p->nx, p->ny, p->nz, sms, 0);
-    if (lw::sweep3d_prepare() != cudaSuccess) {
+    h->wide3d = !h->sugar && !variant && !(p->flags & LW_ONE_COLUMN);
+    if (lw::sweep3d_prepare() != cudaSuccess || (h->wide3d && lw::sweep3d_wide_prepare() != cudaSuccess)) {
       delete h;
       return LW_ECUDA;
+    }
+    if (h->wide3d) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lw::rk_sweep3d_wide_kernel<3>, lw::kV3T,
+                                                        lw::sweep3d_wide_smem()) != cudaSuccess ||
+          per_sm <= 0)
+        per_sm = 1;
+      h->wide3d_per_sm = per_sm;
+      h->sweep3d_rows = lw::sweep3d_wide_rows(p->nx, p->ny, p->nz, sms, per_sm, 0);
+    } else {
+      h->sweep3d_rows = lw::sweep3d_rows(p->nx, p->ny, p->nz, sms, 0);
     }
   }
   h->kind_names.assign(kKindNames, kKindNames + K_COUNT);
@@ -628,7 +660,6 @@ int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
 int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
   if (!h || nsteps < 0) return LW_EINVAL;
   if (!h->initialised) return LW_ESTATE;
-  const int per_step = launches_per_step(h);
   int64_t left = nsteps;
   if (h->use_graphs && !h->profiling) {
     while (left > 0) {
@@ -648,17 +679,17 @@ int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
         if (rc != LW_OK) return rc;
       }
       if (cudaGraphLaunch(*slot, h->stream) != cudaSuccess) return LW_ECUDA;
-      h->launches += (int64_t)per_step * count;
+      h->launches += launches_for(h, count);
       if (!h->frozen) h->parity = (h->parity + count) & 1;
       if (h->sweep || h->sugar) h->cur = (h->cur + count) & 1;
       h->steps += count;
       left -= count;
     }
   } else {
-    for (; left > 0; --left) {
-      enqueue_one(h, h->frozen ? 0 : h->parity);
-      if (!h->frozen) h->parity ^= 1;
-      h->steps += 1;
+    if (left > 0) {
+      enqueue_many(h, h->frozen ? 0 : h->parity, left);
+      if (!h->frozen) h->parity = (int)((h->parity + left) & 1);
+      h->steps += left;
     }
   }
   if (cudaGetLastError() != cudaSuccess) return LW_ECUDA;
@@ -873,7 +904,9 @@ int lbm_wenoc_set_segment_rows(lbm_wenoc* h, int32_t rows) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
     destroy_graphs(h);
-    if (h->sweep3d) h->sweep3d_rows = lw::sweep3d_rows(h->p.nx, h->p.ny, h->p.nz, sms, rows);
+    if (h->sweep3d)
+      h->sweep3d_rows = h->wide3d ? lw::sweep3d_wide_rows(h->p.nx, h->p.ny, h->p.nz, sms, h->wide3d_per_sm, rows)
+                                  : lw::sweep3d_rows(h->p.nx, h->p.ny, h->p.nz, sms, rows);
     if (h->stage2d)
       h->stage2d_rows = h->wide ? lw::stage2d_wide_rows(h->p.nx, h->p.ny, sms, h->wide_per_sm, rows)
                                 : lw::stage2d_rows(h->p.nx, h->p.ny, sms, rows);
@@ -1532,15 +1565,66 @@ int deposit_gradient_impl(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t 
   };
   int cur = 0;
   h->stream = rs.rev;
+  std::vector<cudaGraphExec_t> rev_full(4, nullptr), rev_tail(4, nullptr);
+  struct GraphsGuard {  // destroys the segment graphs once the reverse stream has drained
+    std::vector<cudaGraphExec_t>* v[2];
+    cudaStream_t rev;
+    ~GraphsGuard() {
+      cudaStreamSynchronize(rev);
+      for (auto* g : v)
+        for (cudaGraphExec_t e : *g)
+          if (e) cudaGraphExecDestroy(e);
+    }
+  } graphs_guard{{&rev_full, &rev_tail}, rs.rev};
   for (int64_t sg = G.nseg - 1; sg >= 0; --sg) {
     if (sg >= 1 && (rc = recompute(sg - 1)) != LW_OK) break;
     if (sg != G.nseg - 1 && cudaStreamWaitEvent(rs.rev, rs.rec_done[set_of(sg)], 0) != cudaSuccess) {
       rc = LW_ECUDA;
       break;
     }
-    for (int64_t k = seg_len(sg) - 1; k >= 0 && rc == LW_OK; --k) {
-      rc = adjoint_step<T>(h, step_record<T>(aw, G, set_of(sg), k), f, fr, lg[cur], lg[cur ^ 1]);
-      cur ^= 1;
+    // the segment's reverse steps: replayed from a CUDA graph captured once per (record
+    // set, lambda buffer, length) -- six launches a step with no host gaps between them --
+    // or launched one by one while the per-kernel timing is on
+    const int64_t len = seg_len(sg);
+    if (h->use_graphs && !h->profiling) {
+      const int key = set_of(sg) * 2 + cur;
+      std::vector<cudaGraphExec_t>& cache = len == segment ? rev_full : rev_tail;
+      if (!cache[key]) {
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+          rc = LW_ECUDA;
+          break;
+        }
+        cudaGraph_t gr = nullptr;
+        h->stream = cap;
+        const int64_t saved = h->launches;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int c2 = cur;
+        for (int64_t k = len - 1; k >= 0 && e == cudaSuccess && rc == LW_OK; --k) {
+          rc = adjoint_step<T>(h, step_record<T>(aw, G, set_of(sg), k), f, fr, lg[c2], lg[c2 ^ 1]);
+          c2 ^= 1;
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&cache[key], gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        cudaStreamDestroy(cap);
+        h->stream = rs.rev;
+        h->launches = saved;
+        if (e != cudaSuccess && rc == LW_OK) rc = LW_ECUDA;
+        if (rc != LW_OK) break;
+      }
+      if (cudaGraphLaunch(cache[key], rs.rev) != cudaSuccess) {
+        rc = LW_ECUDA;
+        break;
+      }
+      h->launches += 6 * len;
+      if (len & 1) cur ^= 1;
+    } else {
+      for (int64_t k = len - 1; k >= 0 && rc == LW_OK; --k) {
+        rc = adjoint_step<T>(h, step_record<T>(aw, G, set_of(sg), k), f, fr, lg[cur], lg[cur ^ 1]);
+        cur ^= 1;
+      }
     }
     if (rc != LW_OK) break;
     if (G.nseg > 1 && cudaEventRecord(rs.rev_done[set_of(sg)], rs.rev) != cudaSuccess) {

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kNoAllocThreads) noalloc_sum_kernel(const T* _
 
 // Device address of the scratch array on the current device.  The array's name is
 // only a host-side stand-in in host code, so the address is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached for the life of the process; a device reset
+// (cudaDeviceReset, or the primary context torn down) makes the cached address stale.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LW_ECUDA;

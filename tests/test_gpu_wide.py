@@ -65,3 +65,35 @@ def test_four_column_kernel_segments_bitwise(shape):
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), rows
         assert d == dep, rows
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 40), (36, 20, 24), (96, 40, 70)])
+def test_four_column_3d_kernel_bitwise_equal_to_one_column(shape):
+    # 3D: four x columns per thread on 32 x 16 tiles, ragged in x and y, several z segments
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    c0 = workloads.interface_field(shape, interface_frac=0.6, amplitude=0.03, seed=24)
+    out = {}
+    for one in (False, True):
+        s = lw.Simulation(shape, fp64=False, one_column=one, **STRONG)
+        s.init(c0)
+        s.step(9)
+        out[one] = ([to_np(t) for t in s.fields()], s.deposit)
+    for a, b in zip(out[False][0], out[True][0]):
+        assert np.array_equal(a, b)
+    assert out[False][1] == out[True][1]
+    o = oracle.OracleSim(shape, **STRONG)
+    o.init(c0.astype(np.float32).astype(np.float64))
+    o.step(9)
+    assert rel_l2(out[False][0][2], o.fields()[2]) < 1e-5
+
+
+def test_four_column_3d_kernel_segments_bitwise():
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    shape = (64, 32, 50)
+    c0 = workloads.interface_field(shape, interface_frac=0.5, amplitude=0.03, seed=25)
+    ref, dep = _run(shape, c0, 6)
+    for rows in (1, 3, 7, 32, 200):
+        got, d = _run(shape, c0, 6, rows=rows)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), rows
+        assert d == dep, rows

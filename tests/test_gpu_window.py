@@ -12,10 +12,10 @@ twin of the oracle whose initial c differs by half an FP32 unit in the last plac
 node already drifts 1.3e-5 (relative L2 of c) away from it there.  The test holds:
   * c within 1e-5 relative L2 at every 1000 steps up to step 8000 (mode amplitude below
     0.1 % of its wavelength);
-  * from there to the end of the window (about step 34000), c within the larger of 2.5e-5
-    and 500 x the twin's drift at the same step: the FP32 error first grows by the
-    rounding of each step (1.1e-5 .. 2.0e-5 up to step 15000) and then at the rate of the
-    instability itself, at 240 - 370 x the twin's drift (measured);
+  * from there to the end of the window (step 34000), c within the larger of 2.5e-5 and
+    500 x the twin's drift at the same step: the FP32 error first grows by the rounding of
+    each step (1.1e-5 .. 2.0e-5 up to step 15000, 1450 .. 430 x the still tiny twin drift)
+    and then at the rate of the instability itself, at 240 - 370 x the twin's drift;
   * the deposited mass within 3e-6 throughout (measured 1.5e-6 at most).
 """
 import numpy as np

@@ -52,3 +52,39 @@ def test_noalloc_rejects_fields_beyond_the_scratch():
     assert e.value.code == lw.LW_EINVAL
     with pytest.raises(lw.LbmWenocError):
         lw.lbm_wenoc_total_mass_noalloc(c, 0, False, None, out)
+
+
+@pytest.mark.parametrize("n", [3 * 32768 + 17, 2048 * 32768])
+def test_noalloc_partial_last_block_and_the_limit(n):
+    # several blocks with a partial last one, and the largest accepted size, against an
+    # FP64 sum of the same numbers
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    g = torch.Generator(device="cuda").manual_seed(7)
+    c = torch.rand(n, dtype=torch.float32, device="cuda", generator=g)
+    want = float(c.double().sum().item())
+    out = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    lw.lbm_wenoc_total_mass_noalloc(c, n, False, torch.cuda.current_stream().cuda_stream, out)
+    torch.cuda.synchronize()
+    assert abs(float(out.item()) - want) <= 1e-12 * abs(want)
+    del c
+    torch.cuda.empty_cache()
+
+
+def test_noalloc_calls_on_two_streams_ordered_by_an_event():
+    # The second call, on another stream, waits for the first through an event: the scratch
+    # (its ticket cleared at the start of each call) is then reused safely.
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    a = torch.arange(5 * 32768 + 3, dtype=torch.float32, device="cuda") * 1e-3
+    b = torch.ones(70000, dtype=torch.float32, device="cuda")
+    oa = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    ob = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    lw.lbm_wenoc_total_mass_noalloc(a, a.numel(), False, s1.cuda_stream, oa)
+    ev = torch.cuda.Event()
+    ev.record(s1)
+    s2.wait_event(ev)
+    lw.lbm_wenoc_total_mass_noalloc(b, b.numel(), False, s2.cuda_stream, ob)
+    torch.cuda.synchronize()
+    assert abs(float(oa.item()) - float(a.double().sum().item())) <= 1e-12 * float(a.double().sum().item())
+    assert float(ob.item()) == 70000.0
