@@ -667,6 +667,9 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batch", "adjoint"],
                     help="2d: the 2048x4096 D2Q9 case the metric is quoted on; 3d: 256x256x512 D3Q19; "
                          "sugar: the 2048x4096 case with the sugar scalar; batch; adjoint")
+    ap.add_argument("--lattice", default="",
+                    help="override the lattice, e.g. 256x256x128 (profiling captures of a smaller case only; "
+                         "the line then names the smaller lattice)")
     args = ap.parse_args()
     global WL, METRIC, LATTICE
     if args.workload == "batch":
@@ -684,6 +687,12 @@ def main():
         bench_adjoint(args)
         return
     WL, METRIC, LATTICE = WORKLOADS[args.workload]
+    if args.lattice:
+        shape = tuple(int(v) for v in args.lattice.lower().split("x"))
+        if len(shape) != len(WL.shape):
+            ap.error("--lattice needs as many extents as the workload's lattice")
+        WL = WL.with_(shape=shape, name=f"{WL.name}_as_{args.lattice}")
+        METRIC = METRIC + f" [lattice {args.lattice}]"
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
