@@ -71,6 +71,9 @@ __device__ __forceinline__ T settling_at(const Args<T>& a, long long m) {
   return a.S ? a.vs * (T(1) - a.ks * a.S[m]) : a.vs;
 }
 
+// fused multiply-add of the kernel's precision (fmaf for FP32, fma for FP64)
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ int wrap_dec(int a, int n) { return a < 0 ? a + n : a; }
 __device__ __forceinline__ int wrap_inc(int a, int n) { return a >= n ? a - n : a; }
 __device__ __forceinline__ int wrap_any(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }

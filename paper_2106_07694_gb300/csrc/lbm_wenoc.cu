@@ -358,18 +358,19 @@ void enqueue_transport(lbm_wenoc* h, const Args<T>& a) {
     h->cur ^= 1;
     return;
   }
-  if (std::is_same<T, float>::value && LAT::DIM == 2 && h->stage2d) {
-    const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
+  if (LAT::DIM == 2 && h->stage2d) {
     const int H = h->stage2d_rows;
-    if (h->wide) {
+    if (std::is_same<T, float>::value && h->wide) {
+      const Args<float>& af = reinterpret_cast<const Args<float>&>(a);
       launch(h, K_STAGE1, [&] { lw::launch_stage2d_wide<1>(af, af.c, af.c1, H, s); });
       launch(h, K_STAGE2, [&] { lw::launch_stage2d_wide<2>(af, af.c1, af.c2, H, s); });
       launch(h, K_STAGE3, [&] { lw::launch_stage2d_wide<3>(af, af.c2, af.c, H, s); });  // + deposit
       return;
     }
-    launch(h, K_STAGE1, [&] { lw::launch_stage2d<1>(af, af.c, af.c1, H, s); });
-    launch(h, K_STAGE2, [&] { lw::launch_stage2d<2>(af, af.c1, af.c2, H, s); });
-    launch(h, K_STAGE3, [&] { lw::launch_stage2d<3>(af, af.c2, af.c, H, s); });  // + deposit
+    // one column per thread, FP32 or FP64 (the validation build's 2D path)
+    launch(h, K_STAGE1, [&] { lw::launch_stage2d<1, T>(a, a.c, a.c1, H, s); });
+    launch(h, K_STAGE2, [&] { lw::launch_stage2d<2, T>(a, a.c1, a.c2, H, s); });
+    launch(h, K_STAGE3, [&] { lw::launch_stage2d<3, T>(a, a.c2, a.c, H, s); });  // + deposit
     return;
   }
   if (std::is_same<T, float>::value && LAT::DIM == 3 && h->sweep3d && h->wide3d) {
@@ -553,9 +554,9 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
   h->sweep = !h->fp64 && !variant && h->p.dim == 2 && lw::sweep2d_supported(p->nx, p->ny, h->walls) &&
              (p->flags & LW_FUSED_RK3) != 0;
   // the row-sweep stage kernels take the scheme variants and the sugar scalar too
-  h->stage2d = !h->fp64 && h->p.dim == 2 && h->walls && !h->sweep &&
-               (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
-  h->wide = h->stage2d && !h->sugar && !variant && !(p->flags & LW_ONE_COLUMN);
+  // (FP64 too: the validation build runs the one-column form)
+  h->stage2d = h->p.dim == 2 && h->walls && !h->sweep && (p->nx + lw::kS2T - 1) / lw::kS2T <= lw::kMaxReduceBlocks;
+  h->wide = h->stage2d && !h->fp64 && !h->sugar && !variant && !(p->flags & LW_ONE_COLUMN);
   if (h->stage2d) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 148;

@@ -1,4 +1,4 @@
-// 2D FP32 transport: one SSP-RK3 stage of the WENO5 + diffusion + settling update of c
+// 2D transport (FP32; FP64 in the validation build): one SSP-RK3 stage of the WENO5 + diffusion + settling update of c
 // (steps a4..a8) as a row sweep, the 2D counterpart of the 3D stage kernels.
 //
 // A CTA owns a strip of 128 columns and a segment of rows and sweeps it upward.  At row
@@ -22,46 +22,50 @@ constexpr int kS2h = 3;               // stencil radius
 constexpr int kS2X = kS2T + 2 * kS2h;
 constexpr int kS2r = 6;               // y ring depth (rows k-2 .. k+3), stored twice
 
+template <typename T>
 struct Stage2dSmem {
-  float xp[kS2X];  // x-split h+/alpha of the current row (strip + halo)
-  float xm[kS2X];
-  float c[kS2X];   // stage input value of the current row
-  float yp[2 * kS2r][kS2T];  // y-split ring of each column; slot r and r + 6 hold the same
-  float ym[2 * kS2r][kS2T];  // row, so the six rows of a face are read without wrap-around
-  float cy[2 * kS2r][kS2T];  // stage input value ring of each column, stored the same way
-  float fx[kS2T + 1];    // left x faces (+ right edge)
+  T xp[kS2X];  // x-split h+/alpha of the current row (strip + halo)
+  T xm[kS2X];
+  T c[kS2X];   // stage input value of the current row
+  T yp[2 * kS2r][kS2T];  // y-split ring of each column; slot r and r + 6 hold the same
+  T ym[2 * kS2r][kS2T];  // row, so the six rows of a face are read without wrap-around
+  T cy[2 * kS2r][kS2T];  // stage input value ring of each column, stored the same way
+  T fx[kS2T + 1];    // left x faces (+ right edge)
 };
 
-struct Stage2dParams {
-  const float* cin;  // stage input (c, c1 or c2)
-  float* cout;       // stage output (c1, c2 or c in place)
-  int H;             // rows per segment
+template <typename T>
+struct Stage2dParamsT {
+  const T* cin;  // stage input (c, c1 or c2)
+  T* cout;       // stage output (c1, c2 or c in place)
+  int H;         // rows per segment
 };
+using Stage2dParams = Stage2dParamsT<float>;
 
 // Body of the stage kernel for strip bx, segment by; `strips` = number of strips (the
 // floor CTAs that fold the deposit).  SCHEME: transport-scheme variant bits (kSchemeWeno3,
-// kSchemeSignSplit; 0 = Lax-Friedrichs WENO5), see face_flux_scheme.
-template <int STAGE, bool SUGAR = false, int SCHEME = 0>
-__device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2dParams& sp, int bx, int by,
+// kSchemeSignSplit; 0 = Lax-Friedrichs WENO5), see face_flux_scheme.  T = float (the
+// production path) or double (the validation build: the same sweep in FP64).
+template <int STAGE, bool SUGAR = false, int SCHEME = 0, typename T = float>
+__device__ __forceinline__ void stage2d_body(const Args<T>& a, const Stage2dParamsT<T>& sp, int bx, int by,
                                              int strips) {
-  __shared__ __align__(16) Stage2dSmem S;
+  __shared__ __align__(16) Stage2dSmem<T> S;
   const int t = threadIdx.x;
   const int nx = a.nx, ny = a.ny;
   const int x0 = bx * kS2T;
   const int y0 = by * sp.H, y1 = min(ny, y0 + sp.H);
   const int X = (x0 + t) % nx;
   const bool out = x0 + t < nx;
-  const float inv_alpha = a.inv_alpha, vs_a = a.vs * a.inv_alpha, alpha = a.alpha, kappa = a.kappa;
-  const float* __restrict__ cin = sp.cin;
-  const float* __restrict__ ux = a.u;
-  const float* __restrict__ uy = a.u + a.n;
+  const T inv_alpha = a.inv_alpha, vs_a = a.vs * a.inv_alpha, alpha = a.alpha, kappa = a.kappa;
+  const T* __restrict__ cin = sp.cin;
+  const T* __restrict__ ux = a.u;
+  const T* __restrict__ uy = a.u + a.n;
 
   // staging positions of this thread in the strip + halo row (fixed for the sweep)
   const int j1 = t + kS2T;  // second position, only for the 6 halo columns
   const unsigned gx1 = (unsigned)((x0 - kS2h + j1 + 4 * nx) % nx);
   const unsigned gxs = (unsigned)((x0 - kS2h + t + 4 * nx) % nx);
   const bool has2 = j1 < kS2X;
-  float p0c = 0.f, p0u = 0.f, p1c = 0.f, p1u = 0.f;
+  T p0c = T(0), p0u = T(0), p1c = T(0), p1u = T(0);
   auto fetch_row = [&](int k) {
     if (k >= y1) return;
     const unsigned row = (unsigned)k * (unsigned)nx;
@@ -73,20 +77,20 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
     }
   };
   // own column, row l (ghost rows reflect): value and scaled vertical velocity
-  float qc = 0.f, qw = 0.f, qn = 0.f;
+  T qc = T(0), qw = T(0), qn = T(0);
   auto col_fetch = [&](int l) {
     const bool ghost = l < 0 || l >= ny;
     const int lr = l < 0 ? -1 - l : (l >= ny ? 2 * ny - 1 - l : l);
     const unsigned k = (unsigned)lr * (unsigned)nx + X;
     qc = __ldg(cin + k);
-    const float u = __ldg(uy + k);
+    const T u = __ldg(uy + k);
     // with sugar the settling velocity of the node (a ghost reads its mirror's) is Vs (1 - ks S)
-    const float vsa = SUGAR ? vs_a * fmaf(-a.ks, __ldg(a.S + k), 1.f) : vs_a;
-    qw = fmaf(ghost ? -u : u, inv_alpha, -vsa);
+    const T vsa = SUGAR ? vs_a * fma_t(-a.ks, __ldg(a.S + k), T(1)) : vs_a;
+    qw = fma_t(ghost ? -u : u, inv_alpha, -vsa);
   };
   constexpr bool SIGN = (SCHEME & kSchemeSignSplit) != 0;
   auto col_put = [&](int slot) {
-    const float h = 0.5f * qc, p = SIGN ? qw * qc : fmaf(qw, h, h), m = SIGN ? qw : fmaf(qw, h, -h);
+    const T h = T(0.5) * qc, p = SIGN ? qw * qc : fma_t(qw, h, h), m = SIGN ? qw : fma_t(qw, h, -h);
     S.yp[slot][t] = p;
     S.yp[slot + kS2r][t] = p;
     S.ym[slot][t] = m;
@@ -107,28 +111,28 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
   int slot = (kb + 3) % kS2r;  // ring slot of row k + 3
   fetch_row(kb);
   cn_fetch(kb);
-  float carry = 0.f;
+  T carry = T(0);
   double dep = 0.0;  // stage 3, floor row: this column's Vs-free deposit term
 
   for (int k = kb; k < y1; ++k) {
     const bool prime = k < y0;
     // ---- stage row k (prefetched), own column three rows ahead
     {
-      const float h0 = 0.5f * p0c, w0 = p0u * inv_alpha;
+      const T h0 = T(0.5) * p0c, w0 = p0u * inv_alpha;
       S.c[t] = p0c;
-      S.xp[t] = SIGN ? w0 * p0c : fmaf(w0, h0, h0);
-      S.xm[t] = SIGN ? w0 : fmaf(w0, h0, -h0);
+      S.xp[t] = SIGN ? w0 * p0c : fma_t(w0, h0, h0);
+      S.xm[t] = SIGN ? w0 : fma_t(w0, h0, -h0);
       if (has2) {
-        const float h1 = 0.5f * p1c, w1 = p1u * inv_alpha;
+        const T h1 = T(0.5) * p1c, w1 = p1u * inv_alpha;
         S.c[j1] = p1c;
-        S.xp[j1] = SIGN ? w1 * p1c : fmaf(w1, h1, h1);
-        S.xm[j1] = SIGN ? w1 : fmaf(w1, h1, -h1);
+        S.xp[j1] = SIGN ? w1 * p1c : fma_t(w1, h1, h1);
+        S.xm[j1] = SIGN ? w1 : fma_t(w1, h1, -h1);
       }
     }
     fetch_row(k + 1);
     col_put(slot);
     col_fetch(k + 4);
-    const float cn_here = qn;
+    const T cn_here = qn;
     cn_fetch(k + 1);
     __syncthreads();
 
@@ -146,7 +150,7 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
         }
       } else {
         auto xface = [&](int j) {  // face between staging positions j + 2 and j + 3
-          float p[6], m[6];
+          T p[6], m[6];
 #pragma unroll
           for (int q = 0; q < 6; ++q) {
             p[q] = S.xp[j + q];
@@ -159,16 +163,16 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
       }
     }
     const int rb = slot == kS2r - 1 ? 0 : slot + 1;  // ring slot of row k - 2 (= that of row k + 4)
-    const float chere = S.cy[rb + 2][t], cnext = S.cy[rb + 3][t];
-    float fup = 0.f;
+    const T chere = S.cy[rb + 2][t], cnext = S.cy[rb + 3][t];
+    T fup = T(0);
     if (k != ny - 1) {
-      const float* P = &S.yp[rb][t];
-      const float* M = &S.ym[rb][t];
+      const T* P = &S.yp[rb][t];
+      const T* M = &S.ym[rb][t];
       if constexpr (SCHEME == 0) {
         fup = face_flux_x(P[0], P[kS2T], P[2 * kS2T], P[3 * kS2T], P[4 * kS2T], M[5 * kS2T], M[4 * kS2T],
                           M[3 * kS2T], M[2 * kS2T], M[kS2T], alpha, kappa, chere, cnext);
       } else {
-        float p[6], m[6];
+        T p[6], m[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           p[q] = P[q * kS2T];
@@ -181,18 +185,18 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
 
     // ---- divergence and the Shu-Osher combination of this stage
     if (!prime) {
-      const float vs_floor = SUGAR && k == 0 ? a.vs * fmaf(-a.ks, __ldg(a.S + X), 1.f) : a.vs;
-      const float fdn = k == 0 ? -vs_floor * chere : carry;
-      const float L = S.fx[t] - S.fx[t + 1] + fdn - fup;
+      const T vs_floor = SUGAR && k == 0 ? a.vs * fma_t(-a.ks, __ldg(a.S + X), T(1)) : a.vs;
+      const T fdn = k == 0 ? -vs_floor * chere : carry;
+      const T L = S.fx[t] - S.fx[t + 1] + fdn - fup;
       if (out) {
-        float v;
+        T v;
         if (STAGE == 1) {
           v = chere + L;
         } else if (STAGE == 2) {
-          v = fmaf(0.75f, cn_here, 0.25f * (chere + L));
+          v = fma_t(T(0.75), cn_here, T(0.25) * (chere + L));
         } else {
-          const float s = chere + L;
-          v = fmaf(1.f / 3.f, cn_here - s, s);
+          const T s = chere + L;
+          v = fma_t(T(1) / T(3), cn_here - s, s);
         }
         sp.cout[(unsigned)k * (unsigned)nx + X] = v;
         if (STAGE == 3) {
@@ -237,9 +241,9 @@ __device__ __forceinline__ void stage2d_body(const Args<float>& a, const Stage2d
   }
 }
 
-template <int STAGE, bool SUGAR = false, int SCHEME = 0>
-__global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<float> a, Stage2dParams sp) {
-  stage2d_body<STAGE, SUGAR, SCHEME>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
+template <int STAGE, bool SUGAR = false, int SCHEME = 0, typename T = float>
+__global__ void __launch_bounds__(kS2T) rk_stage2d_kernel(Args<T> a, Stage2dParamsT<T> sp) {
+  stage2d_body<STAGE, SUGAR, SCHEME, T>(a, sp, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
@@ -255,34 +259,34 @@ inline int stage2d_rows(int nx, int ny, int sm_count, int override_rows) {
 }
 
 // The stage kernel of the handle's transport scheme (runtime field) as a compile-time variant.
-template <int STAGE, bool SUGAR>
-inline void launch_stage2d_scheme(const Args<float>& a, const Stage2dParams& sp, dim3 grid, cudaStream_t s) {
+template <int STAGE, bool SUGAR, typename T>
+inline void launch_stage2d_scheme(const Args<T>& a, const Stage2dParamsT<T>& sp, dim3 grid, cudaStream_t s) {
   switch (a.scheme) {
     case kSchemeWeno3:
-      rk_stage2d_kernel<STAGE, SUGAR, kSchemeWeno3><<<grid, kS2T, 0, s>>>(a, sp);
+      rk_stage2d_kernel<STAGE, SUGAR, kSchemeWeno3, T><<<grid, kS2T, 0, s>>>(a, sp);
       break;
     case kSchemeSignSplit:
-      rk_stage2d_kernel<STAGE, SUGAR, kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
+      rk_stage2d_kernel<STAGE, SUGAR, kSchemeSignSplit, T><<<grid, kS2T, 0, s>>>(a, sp);
       break;
     case kSchemeWeno3 | kSchemeSignSplit:
-      rk_stage2d_kernel<STAGE, SUGAR, kSchemeWeno3 | kSchemeSignSplit><<<grid, kS2T, 0, s>>>(a, sp);
+      rk_stage2d_kernel<STAGE, SUGAR, kSchemeWeno3 | kSchemeSignSplit, T><<<grid, kS2T, 0, s>>>(a, sp);
       break;
     default:
-      rk_stage2d_kernel<STAGE, SUGAR><<<grid, kS2T, 0, s>>>(a, sp);
+      rk_stage2d_kernel<STAGE, SUGAR, 0, T><<<grid, kS2T, 0, s>>>(a, sp);
   }
 }
 
-template <int STAGE>
-inline cudaError_t launch_stage2d(const Args<float>& a, const float* cin, float* cout, int H, cudaStream_t s) {
-  Stage2dParams sp;
+template <int STAGE, typename T>
+inline cudaError_t launch_stage2d(const Args<T>& a, const T* cin, T* cout, int H, cudaStream_t s) {
+  Stage2dParamsT<T> sp;
   sp.cin = cin;
   sp.cout = cout;
   sp.H = H;
   const dim3 grid((a.nx + kS2T - 1) / kS2T, (a.ny + H - 1) / H);
   if (a.S)
-    launch_stage2d_scheme<STAGE, true>(a, sp, grid, s);
+    launch_stage2d_scheme<STAGE, true, T>(a, sp, grid, s);
   else
-    launch_stage2d_scheme<STAGE, false>(a, sp, grid, s);
+    launch_stage2d_scheme<STAGE, false, T>(a, sp, grid, s);
   return cudaGetLastError();
 }
 

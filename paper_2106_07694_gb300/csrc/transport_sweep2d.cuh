@@ -85,19 +85,51 @@ __device__ __forceinline__ float weno3_face_value(float a, float b, float c) {
   return __fdividef(fmaf(p1, b + c, a1 * fmaf(3.f, b, -a)), 2.f * (p1 + a1));
 }
 
+// FP64 forms of the same face values (the validation build): the same algebra with fma
+// and an IEEE division.
+__device__ __forceinline__ double weno5_q(double d1, double d2, double d3, double d4, double s0, double s1,
+                                          double s2) {
+  const double t0 = fma(3.0, d2, -d1), t1 = d2 + d3, t2 = fma(-3.0, d3, d4);
+  const double q = 3.0 / 13.0, eps = 1e-6 * (12.0 / 13.0);
+  double A0 = fma(s0, s0, fma(q * t0, t0, eps));
+  double A1 = fma(s1, s1, fma(q * t1, t1, eps));
+  double A2 = fma(s2, s2, fma(q * t2, t2, eps));
+  A0 *= A0;
+  A1 *= A1;
+  A2 *= A2;
+  const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(4.0, d3, -d4);
+  const double A02x6 = 6.0 * (A0 * A2);
+  const double num = fma(A1, fma(3.0 * A0, r2, A2 * r0), A02x6 * r1);
+  const double den = fma(A1, fma(3.0, A0, A2), A02x6);
+  return num / den;
+}
+
+__device__ __forceinline__ double weno5_face_value(double a, double b, double c, double d, double e) {
+  const double d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
+  return fma(weno5_q(d1, d2, d3, d4, d2 - d1, d3 - d2, d4 - d3), 1.0 / 6.0, c);
+}
+
+__device__ __forceinline__ double weno3_face_value(double a, double b, double c) {
+  const double eps = 1e-6;
+  double a1 = fma(c - b, c - b, eps), a2 = fma(b - a, b - a, eps);
+  a1 *= a1;
+  a2 *= a2;
+  const double p1 = 2.0 * a2;
+  return fma(p1, b + c, a1 * fma(3.0, b, -a)) / (2.0 * (p1 + a1));
+}
+
 // Face flux of a transport-scheme variant (SCHEME = kSchemeWeno3 | kSchemeSignSplit bits;
 // 0 is the Lax-Friedrichs WENO5 of face_flux_x) from the staged pairs of the six points
 // i-2 .. i+3 around the face i+1/2 (p[k], m[k] = point i-2+k).  Lax-Friedrichs schemes
 // stage p = h+/alpha, m = h-/alpha; the sign split stages p = w c/alpha, m = w/alpha and
 // reconstructs w c from the side the face velocity (w_i + w_{i+1})/2 comes from (ties
-// to the left).
-template <int SCHEME>
-__device__ __forceinline__ float face_flux_scheme(const float (&p)[6], const float (&m)[6], float alpha,
-                                                  float kappa, float cl, float cr) {
+// to the left).  T = float or double.
+template <int SCHEME, typename T>
+__device__ __forceinline__ T face_flux_scheme(const T (&p)[6], const T (&m)[6], T alpha, T kappa, T cl, T cr) {
   constexpr bool W3 = (SCHEME & kSchemeWeno3) != 0, SIGN = (SCHEME & kSchemeSignSplit) != 0;
-  float h;
+  T h;
   if (SIGN) {
-    const bool left = m[2] + m[3] >= 0.f;
+    const bool left = m[2] + m[3] >= T(0);
     if (W3) {
       h = weno3_face_value(left ? p[1] : p[4], left ? p[2] : p[3], left ? p[3] : p[2]);
     } else {
@@ -109,17 +141,17 @@ __device__ __forceinline__ float face_flux_scheme(const float (&p)[6], const flo
   } else {
     h = weno5_face_value(p[0], p[1], p[2], p[3], p[4]) + weno5_face_value(m[5], m[4], m[3], m[2], m[1]);
   }
-  return fmaf(alpha, h, kappa * (cl - cr));
+  return fma_t(alpha, h, kappa * (cl - cr));
 }
 
 // Total face flux (unscaled): alpha (h+ + h-) + kappa (cl - cr), with h+ from the
 // left-biased values p0..p4 and h- from the right-biased values m0..m4 (already mirrored).
-__device__ __forceinline__ float face_flux_x(float p0, float p1, float p2, float p3, float p4, float m0,
-                                            float m1, float m2, float m3, float m4, float alpha, float kappa,
-                                            float cl, float cr) {
-  const float hp = weno5_face_value(p0, p1, p2, p3, p4);
-  const float hm = weno5_face_value(m0, m1, m2, m3, m4);
-  return fmaf(alpha, hp + hm, kappa * (cl - cr));
+template <typename T>
+__device__ __forceinline__ T face_flux_x(T p0, T p1, T p2, T p3, T p4, T m0, T m1, T m2, T m3, T m4, T alpha, T kappa,
+                                         T cl, T cr) {
+  const T hp = weno5_face_value(p0, p1, p2, p3, p4);
+  const T hm = weno5_face_value(m0, m1, m2, m3, m4);
+  return fma_t(alpha, hp + hm, kappa * (cl - cr));
 }
 
 // ---------------------------------------------------------------- geometry / smem

@@ -1,0 +1,145 @@
+"""FP32 against the FP64 build on the same GPU over the buoyancy x settling-velocity grid
+A in {1e-5, 2e-5, 5e-5} x Vs in {5e-4, 1e-3, 2e-3} (tau = 0.6, kappa = 1e-3, seed 0,
+interface at 3/4 height, 20000 steps).  The default point (A = 1e-5, Vs = 1e-3) runs on the
+full 2048 x 4096 lattice; the other eight run on 512 x 1024 (an FP64 step of the full
+lattice takes 13 ms, so eight more full-size points would add 37 minutes; they run with
+LW_CFG2_FULL_GRID=1).
+
+Every 100 steps both runs give the lowest front height h_min(t) (the lowest node with
+c = 1/2 over all columns, Sec. 4.1), the deposited mass m_b(t) (Sec. 4.2) and the relative
+L2 distance of c.  Asserted:
+  * finger velocity, the least-squares slope of h_min(t) over the second half of the
+    compared span: within 2 %;
+  * m_b(t) within 2 % of the curve's range at every sample;
+  * both runs leave the model's velocity range (|u| > u_cap = 0.1, LW_EUNSTABLE) in the
+    same 100-step window, or neither does; the comparison ends at the last sample before
+    (A = 5e-5 on 512 x 1024: near step 17000, in both precisions);
+  * c within 2e-4 relative L2 while the dominant front mode is below 1 % of its wavelength.
+    Beyond that the Rayleigh-Taylor growth amplifies any rounding difference (the FP32-FP64
+    distance follows the mode amplitude up, 9e-4 at A = 2e-5 and 1e-2 at A = 5e-5 by the
+    end, with the mode still below 40 % of its wavelength), so only the statistics above
+    are compared there.  In the linear regime the distance is the FP32 rounding of 20000
+    steps: 6.1e-5 at step 20000 of the default point, where an FP64 twin started half an
+    FP32 ulp away drifts only 8e-8 from the FP64 run.
+
+Within 20000 steps the fingers do not reach the floor at these sizes (the lowest front stays
+above 580 of 1024 rows, 3030 of 4096), so m_b(t) here is the settling flux of the initial
+noise below the interface; the deposit of fingers that reach the floor is compared with the
+oracle on 128 x 256 in test_gpu_statistics.py.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lsa
+from paper_2106_07694_gb300 import workloads
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+torch = pytest.importorskip("torch")
+
+STEPS, EVERY = 20000, 100
+DEFAULT = (1e-5, 1e-3)
+OTHERS = [p for p in workloads.MAIN_2D_SWEEP if p != DEFAULT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_07694_gb300 import build
+    build.build()
+
+
+def front_heights(c):
+    """lsa.front_height on the device: per column the lowest height where c reaches 1/2,
+    linearly interpolated, node v at height v + 1/2; c indexed [y][x]."""
+    j = torch.argmax((c >= 0.5).to(torch.int32), dim=0)
+    cj = c.gather(0, j[None]).squeeze(0)
+    cm = c.gather(0, (j - 1).clamp(min=0)[None]).squeeze(0)
+    h = (j - 1).double() + (0.5 - cm) / (cj - cm) + 0.5
+    return torch.where(j == 0, torch.full_like(h, 0.5), h)
+
+
+def mode_ratio(h):
+    """Largest ratio of a front-height mode's amplitude 2|H(k)|/nx to its wavelength nx/k."""
+    nx = h.size
+    H = np.fft.rfft(h - h.mean())
+    k = np.arange(1, H.size)
+    return float(np.max((2 * np.abs(H[1:]) / nx) / (nx / k)))
+
+
+def _curves(shape, A, vs):
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    kw = dict(tau=0.6, gravity=A, density_contrast=1.0, settling_velocity=vs, diffusivity=1e-3)
+    c0 = workloads.MAIN_2D.with_(shape=shape).initial_c().astype(np.float32).astype(np.float64)
+    sims = {p: lw.Simulation(shape, fp64=(p == "f64"), **kw) for p in ("f32", "f64")}
+    for s in sims.values():
+        s.init(c0)
+    cbuf = {p: torch.empty(s.grid, dtype=s.dtype, device="cuda") for p, s in sims.items()}
+    out = {k: [] for k in ("t", "h32", "h64", "m32", "m64", "rel", "psd")}
+    left = {}
+    last_c = {}
+    for k in range(1, STEPS // EVERY + 1):
+        row = {}
+        for p, s in sims.items():
+            s.step(EVERY)
+            try:
+                row[p] = s.deposit
+            except lw.LbmWenocError as e:
+                assert e.code == lw.LW_EUNSTABLE, e
+                left[p] = k * EVERY
+        if left:
+            break
+        cs = {}
+        for p, s in sims.items():
+            lw.lbm_wenoc_fields(s.handle, None, None, cbuf[p])
+            cs[p] = cbuf[p].double()
+        h32, h64 = front_heights(cs["f32"]), front_heights(cs["f64"])
+        out["t"].append(k * EVERY)
+        out["h32"].append(float(h32.min()))
+        out["h64"].append(float(h64.min()))
+        out["m32"].append(row["f32"])
+        out["m64"].append(row["f64"])
+        out["rel"].append(float(torch.linalg.vector_norm(cs["f32"] - cs["f64"]) / torch.linalg.vector_norm(cs["f64"])))
+        out["psd"].append(mode_ratio(h64.cpu().numpy()))
+        last_c = cs
+    res = {k: np.array(v) for k, v in out.items()}
+    res["left"] = left
+    res["last_c64"] = last_c["f64"].cpu().numpy()
+    return res
+
+
+def _check(shape, A, vs):
+    r = _curves(shape, A, vs)
+    # both precisions leave the velocity range in the same window, or neither does
+    assert set(r["left"]) in (set(), {"f32", "f64"}), r["left"]
+    t = r["t"]
+    assert t.size >= 100, "the compared span is shorter than 10000 steps"
+    # the device front heights are lsa.front_height's
+    c = r["last_c64"]
+    assert np.allclose(front_heights(torch.from_numpy(c)).numpy(), lsa.front_height(c), rtol=0, atol=1e-9)
+    # finger velocity: slope of the lowest front over the second half of the span
+    sel = t > t[-1] / 2
+    v32 = np.polyfit(t[sel], r["h32"][sel], 1)[0]
+    v64 = np.polyfit(t[sel], r["h64"][sel], 1)[0]
+    assert v64 < 0 and abs(v32 - v64) <= 0.02 * abs(v64), (v32, v64)
+    # deposited mass curve
+    span = r["m64"].max() - r["m64"].min()
+    assert span > 0 and np.abs(r["m32"] - r["m64"]).max() <= 0.02 * span
+    # element-wise while the front is linear
+    lin = r["psd"] < 1e-2
+    assert lin[0] and np.all(r["rel"][lin] <= 2e-4), r["rel"][lin].max()
+    print(f"A={A} Vs={vs} {shape}: span {t[-1]} steps, finger velocity {v32:.4e} / {v64:.4e}, "
+          f"m_b max diff {np.abs(r['m32'] - r['m64']).max():.2e} of {span:.3e}, "
+          f"c rel L2 {r['rel'][lin].max():.2e} (linear) {r['rel'].max():.2e} (all), mode {r['psd'].max():.3f}")
+
+
+def test_default_point_full_lattice_fp32_matches_fp64_statistics():
+    _check((2048, 4096), *DEFAULT)
+
+
+@pytest.mark.parametrize("A,vs", OTHERS)
+def test_sweep_grid_fp32_matches_fp64_statistics(A, vs):
+    full = os.environ.get("LW_CFG2_FULL_GRID") == "1"
+    _check((2048, 4096) if full else (512, 1024), A, vs)

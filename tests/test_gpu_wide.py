@@ -97,3 +97,28 @@ def test_four_column_3d_kernel_segments_bitwise():
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), rows
         assert d == dep, rows
+
+
+@pytest.mark.parametrize("shape", [(260, 90), (128, 64)])
+def test_fp64_row_sweep_segments_bitwise(shape):
+    # the FP64 build runs the same one-column row sweep: segment heights change nothing,
+    # and it stays on the FP64 oracle to rounding
+    from paper_2106_07694_gb300 import lbm_wenoc as lw
+    c0 = workloads.interface_field(shape, interface_frac=0.5, amplitude=0.03, seed=26)
+    out = []
+    for rows in (0, 1, 3, 16, 200):
+        s = lw.Simulation(shape, fp64=True, **STRONG)
+        if rows:
+            lw.lbm_wenoc_set_segment_rows(s.handle, rows)
+        s.init(c0)
+        s.step(10)
+        out.append(([to_np(t) for t in s.fields()], s.deposit))
+    for got, d in out[1:]:
+        for a, b in zip(got, out[0][0]):
+            assert np.array_equal(a, b)
+        assert d == out[0][1]
+    o = oracle.OracleSim(shape, **STRONG)
+    o.init(c0)
+    o.step(10)
+    assert rel_l2(out[0][0][2], o.fields()[2]) < 1e-12
+    assert abs(out[0][1] - o.deposit) <= 1e-12 * abs(o.deposit)
