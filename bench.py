@@ -158,20 +158,29 @@ class ClockSampler:
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/, with the SHA-1 prefix of the kernel sources they were
-# taken on (the kernel's file and the headers it includes, concatenated in this order); a
-# changed kernel reports null until it is captured again.
+# launch lists summarised in profiles/ (the bench command itself, one pass per launch), with
+# the SHA-1 prefix of the kernel sources they were taken on (the kernel's file and the
+# headers it includes, concatenated in this order); a changed kernel reports null until it
+# is captured again.  The fluid entry is the mean of the two AA parities.
 _CSRC = "paper_2106_07694_gb300/csrc/"
 _LBM_SRC = ("lbm_kernels.cuh", "lattice.cuh", "common.cuh")
 _STAGE_SRC = ("transport_stage2d_wide.cuh", "transport_stage2d.cuh", "transport_sweep2d.cuh", "reduce_kernels.cuh",
               "common.cuh")
+_STAGE3D_SRC = ("transport_sweep3d_wide.cuh", "transport_sweep3d.cuh") + _STAGE_SRC
 NCU_TRAFFIC = {
-    "lbm_collide_stream": (643.15e6, _LBM_SRC, "916b01ee7eb7"),
-    "rk_stage1": (112.97e6, _STAGE_SRC, "a94c5aff49b3"),
-    "rk_stage2": (150.55e6, _STAGE_SRC, "a94c5aff49b3"),
-    "rk_stage3": (146.62e6, _STAGE_SRC, "a94c5aff49b3"),
+    "lbm_collide_stream": (642.85e6, _LBM_SRC, "a206248f2c9f"),
+    "rk_stage1": (134.2e6, _STAGE_SRC, "205753d759ef"),
+    "rk_stage2": (179.1e6, _STAGE_SRC, "205753d759ef"),
+    "rk_stage3": (173.4e6, _STAGE_SRC, "205753d759ef"),
     # 512 x 1024 adjoint workload (the face records stay in L2)
     "adj_faces": (8.61e6, ("adjoint.cuh",) + _LBM_SRC, "66654c95daaa"),
+}
+# the 256 x 256 x 512 D3Q19 workload
+NCU_TRAFFIC_3D = {
+    "lbm_collide_stream": (5577.8e6, _LBM_SRC, "a206248f2c9f"),
+    "rk_stage1": (967.7e6, _STAGE3D_SRC, "b11289c97914"),
+    "rk_stage2": (1127.9e6, _STAGE3D_SRC, "b11289c97914"),
+    "rk_stage3": (1108.8e6, _STAGE3D_SRC, "b11289c97914"),
 }
 
 
@@ -184,10 +193,11 @@ def source_hash(files):
     return h.hexdigest()[:12]
 
 
-def kernel_traffic(name):
-    if name not in NCU_TRAFFIC:
+def kernel_traffic(name, table=None):
+    table = NCU_TRAFFIC if table is None else table
+    if name not in table:
         return None
-    nbytes, files, sha = NCU_TRAFFIC[name]
+    nbytes, files, sha = table[name]
     try:
         cur = source_hash(files)
     except OSError:
@@ -345,7 +355,12 @@ def bench_ours(args):
     sms = sm_count(dev)
     fp32_peak = fp32_peak_tflops(clk, sms)
     # ncu traffic was captured on the plain 2D workload's kernels only
-    ncu_traffic = {k: kernel_traffic(k) if wl is workloads.MAIN_2D else None for k in NCU_TRAFFIC}
+    if wl is workloads.MAIN_2D:
+        ncu_traffic = {k: kernel_traffic(k) for k in NCU_TRAFFIC}
+    elif wl is workloads.MAIN_3D:
+        ncu_traffic = {k: kernel_traffic(k, NCU_TRAFFIC_3D) for k in NCU_TRAFFIC_3D}
+    else:
+        ncu_traffic = {}
 
     def avg_s(name):
         n_, t_ = stats[name]
