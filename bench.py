@@ -173,7 +173,7 @@ NCU_TRAFFIC = {
     "rk_stage2": (179.1e6, _STAGE_SRC, "205753d759ef"),
     "rk_stage3": (173.4e6, _STAGE_SRC, "205753d759ef"),
     # 512 x 1024 adjoint workload (the face records stay in L2)
-    "adj_faces": (8.61e6, ("adjoint.cuh",) + _LBM_SRC, "66654c95daaa"),
+    "adj_faces": (8.55e6, ("adjoint.cuh",) + _LBM_SRC, "cf3163dcd081"),
 }
 # the 256 x 256 x 512 D3Q19 workload
 NCU_TRAFFIC_3D = {
