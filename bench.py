@@ -42,6 +42,10 @@ WORKLOADS = {
 WL, METRIC, LATTICE = WORKLOADS["2d"]
 ADJOINT_METRIC = ("gradient of the deposited mass wrt c0 and Vs, GLUPS of the reverse-mode pass "
                   "(2D D2Q9 512x1024 FP32, 2000 steps, checkpoint every 100)")
+# launch form of the batched sweep (lbm_wenoc_batch_set_persistent): 1 all phases in one
+# persistent launch per 16 steps, 2 grouped fluid launch + persistent stage launch per step
+BATCH_MODE = 1
+BATCH_FORMS = {0: "grouped", 1: "persistent", 2: "split"}
 BATCH_METRIC = "coupled LBM+WENO5 GLUPS, batched sweep of 64 D2Q9 FP32 instances (256x512..1024x2048)"
 UNIT = "GLUPS"
 
@@ -490,6 +494,7 @@ def bench_batch(args):
     specs = [dict(shape=w.shape, **phys_kwargs(w)) for w in wls]
     nodes = sum(w.nodes for w in wls)
     b = lw.Batch(specs)
+    b.set_persistent(BATCH_MODE)
     rows = b.autotune(8)
     for inst, w in zip(b.instances, wls):
         inst.init(torch.from_numpy(w.initial_c().astype(np.float32)).cuda())
@@ -509,18 +514,24 @@ def bench_batch(args):
     if b.status() != lw.LW_OK:
         raise RuntimeError("device status set in the batched run")
     value = nodes * args.steps / (ms * 1e-3) / 1e9
-    # the same batch with one launch per kernel type and step instead of the persistent launch
-    b.set_persistent(False)
-    b.step(args.warmup)
-    torch.cuda.synchronize()
-    e0.record()
-    b.step(args.steps)
-    e1.record()
-    torch.cuda.synchronize()
-    grouped_ms = e0.elapsed_time(e1)
-    if b.status() != lw.LW_OK:
-        raise RuntimeError("device status set in the grouped batched run")
+    # the same batch in the other launch forms: all phases persistent (one launch per 16
+    # steps), split (grouped fluid launch + persistent stage launch per step), grouped
+    other_ms = {}
+    for mode in (1, 2, 0):
+        if mode == BATCH_MODE:
+            continue
+        b.set_persistent(mode)
+        b.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record()
+        b.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        other_ms[mode] = e0.elapsed_time(e1)
+        if b.status() != lw.LW_OK:
+            raise RuntimeError(f"device status set in the batched run of form {mode}")
     b.close()
+    grouped_ms = other_ms[0]
     # sequential: the same instances one after the other, same number of steps each
     seq_ms = 0.0
     for w, sp in zip(wls, specs):
@@ -547,6 +558,9 @@ def bench_batch(args):
         "grouped": {"value": nodes * args.steps / (grouped_ms * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": grouped_ms / args.steps,
                     "note": "same batch, one launch per kernel type and step instead of the persistent launch"},
+        "launch_form": BATCH_FORMS[BATCH_MODE],
+        "other_forms": {BATCH_FORMS[m]: {"value": nodes * args.steps / (t_ * 1e-3) / 1e9, "unit": UNIT,
+                                         "ms_per_step": t_ / args.steps} for m, t_ in other_ms.items()},
         "batched_over_sequential": value / seq,
         "step_roofline": {"bound": "hbm", "alg_bytes_per_node": 80, "achieved": 80 * value, "peak": peak,
                           "unit": "GB/s", "frac": 80 * value / peak},

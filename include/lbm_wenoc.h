@@ -201,8 +201,9 @@ lbm_wenoc* lbm_wenoc_batch_instance(lbm_wenoc_batch* b, int32_t i);
 int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps);
 
 /* persistent = 1: the persistent launch (default where the device supports cooperative
- * launches; else LW_EINVAL); 0: one launch per kernel type and step.  Same results.
- * Synchronises the stream; drops captured graphs. */
+ * launches; else LW_EINVAL); 2: per step the fluid part as one grouped launch, then the
+ * three RK3 stages in one persistent launch; 0: one launch per kernel type and step.
+ * Same results; other values LW_EINVAL.  Synchronises the stream; drops captured graphs. */
 int lbm_wenoc_batch_set_persistent(lbm_wenoc_batch* b, int32_t persistent);
 
 /* Bound of a grid-barrier wait of the persistent launch, in SM clock cycles (default

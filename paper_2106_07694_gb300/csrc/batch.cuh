@@ -6,7 +6,7 @@
 // once advances every instance by up to kPersistSteps steps.  A step is four phases --
 // the fluid part (collide-stream), then the three RK3 stages of the transport -- over a
 // work list of (instance, tile) items; a grid barrier separates the phases.  Fluid items
-// are one row by 256 columns, dealt round-robin (uniform cost); stage items are one
+// are one row by 256 columns, one contiguous run per CTA (uniform cost); stage items are one
 // four-column-kernel strip by one row segment (the segment height is the instance's own,
 // chosen by the autotuner), taken from a per-phase counter so that uneven items balance.
 // The barrier waits on a generation word with a clock64 bound: a CTA that waits longer
@@ -15,9 +15,14 @@
 // Every field the launch writes is read back at L2 (LoadL2): L1 is not coherent between
 // SMs within a launch.
 //
+// Split form: per step the fluid part as one grouped launch (below; a short memory-bound
+// kernel with 128-thread CTAs keeps more bytes in flight than the persistent CTAs, whose
+// registers are sized for the stage body), then the three RK3 stages in one persistent
+// launch as above.
+//
 // Grouped form: one launch per kernel type and step; block b finds its instance by a
 // binary search in the prefix table of block counts and runs the single-instance body.
-// Both forms run the same per-node arithmetic as the single-instance kernels.
+// All forms run the same per-node arithmetic as the single-instance kernels.
 #pragma once
 #include "common.cuh"
 #include "lbm_kernels.cuh"
@@ -136,44 +141,72 @@ __device__ __forceinline__ bool batch_grid_sync(const BatchTables& t, unsigned n
   return s_ok != 0;
 }
 
-// Fluid phase of every instance: item = one row by 256 columns (fluid_rows.cuh), dealt
-// round-robin over the CTAs, the next item's windows copied while the current one is
-// collided; the two window buffers overlay the stage phases' shared block.
-// the stage phases' block and the fluid phase's windows share one shared-memory buffer
+// Fluid phase of every instance: item = one row by 256 columns (fluid_rows.cuh); the two
+// window buffers overlay the stage phases' shared block.
 constexpr size_t kPersistSmem = sizeof(StageWideSmem) > sizeof(FluidStage) ? sizeof(StageWideSmem) : sizeof(FluidStage);
 
-template <int PARITY>
-__device__ __forceinline__ void fluid_issue(const BatchTables& t, int item, FluidStage& st, int buf) {
+// Instance of a run of fluid items, kept while the items stay in it: a CTA's items are
+// consecutive, so the table lookup (a chain of dependent loads) is rare.
+struct FluidCursor {
+  int start = 0, end = 0, i = -1, chunks = 1;
+  const float* G = nullptr;
+  const float* C = nullptr;
+  unsigned n = 0;
+  int nx = 0, ny = 0;
+};
+
+__device__ __forceinline__ void fluid_seek(const BatchTables& t, FluidCursor& c, int item) {
+  if (item >= c.start && item < c.end) return;
   const int i = find_instance(t.fl_start, t.count, item);
+  c.i = i;
+  c.start = __ldg(t.fl_start + i);
+  c.end = __ldg(t.fl_start + i + 1);
+  c.chunks = __ldg(t.fl_chunks + i);
   const Args<float>* A = t.args + i;
-  const int local = item - __ldg(t.fl_start + i);
-  const int chunks = __ldg(t.fl_chunks + i);
-  fluid_issue_row<PARITY>(A->g, A->c, (unsigned)A->n, A->nx, A->ny, local / chunks, (local % chunks) * kFluidCols,
-                          st, buf);
+  c.G = A->g;
+  c.C = A->c;
+  c.n = (unsigned)A->n;
+  c.nx = A->nx;
+  c.ny = A->ny;
 }
 
+template <int PARITY>
+__device__ __forceinline__ void fluid_issue(const BatchTables& t, FluidCursor& c, int item, FluidStage& st, int buf) {
+  fluid_seek(t, c, item);
+  const int local = item - c.start;
+  fluid_issue_row<PARITY>(c.G, c.C, c.n, c.nx, c.ny, local / c.chunks, (local % c.chunks) * kFluidCols, st, buf);
+}
+
+// Fluid items are uniform in cost, so each CTA takes one contiguous run of them (rows of
+// one instance in order, which also keeps a row's windows in L2 for the next row's odd-step
+// pulls); the next item's windows are copied while the current one is collided.
 template <int PARITY>
 __device__ __forceinline__ void batch_fluid_phase(const BatchTables& t, FluidStage& st, Args<float>& sa,
                                                   int& s_inst) {
   const int total = __ldg(t.fl_start + t.count);
-  int item = blockIdx.x, buf = 0;
-  if (item < total) fluid_issue<PARITY>(t, item, st, 0);
+  const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int first = (int)blockIdx.x * per, last = min(total, first + per);
+  FluidCursor ci, cc;  // the issuing side (one item ahead) and the computing side
+  int inst = s_inst;   // the instance in sa (the same in every thread)
+  int buf = 0;
+  if (first < last) fluid_issue<PARITY>(t, ci, first, st, 0);
   cp_async_commit();
-  for (; item < total; item += gridDim.x, buf ^= 1) {
-    const int next = item + (int)gridDim.x;
-    if (next < total) fluid_issue<PARITY>(t, next, st, buf ^ 1);
+  for (int item = first; item < last; ++item, buf ^= 1) {
+    if (item + 1 < last) fluid_issue<PARITY>(t, ci, item + 1, st, buf ^ 1);
     cp_async_commit();
     cp_async_wait<1>();  // this item's windows (the next item's copies may still fly)
-    const int i = find_instance(t.fl_start, t.count, item);
-    __syncthreads();  // every thread's copies have landed; sa and s_inst are free to change
-    if (threadIdx.x == 0 && i != s_inst) {
-      sa = t.args[i];
-      s_inst = i;
+    fluid_seek(t, cc, item);
+    __syncthreads();     // every thread's copies have landed; sa is no longer read
+    if (cc.i != inst) {  // uniform: every thread computed the same cursor
+      if (threadIdx.x == 0) {
+        sa = t.args[cc.i];
+        s_inst = cc.i;
+      }
+      inst = cc.i;
+      __syncthreads();
     }
-    __syncthreads();
-    const int local = item - __ldg(t.fl_start + i);
-    const int chunks = __ldg(t.fl_chunks + i);
-    fluid_compute_row<PARITY>(sa, local / chunks, (local % chunks) * kFluidCols, st, buf);
+    const int local = item - cc.start;
+    fluid_compute_row<PARITY>(sa, local / cc.chunks, (local % cc.chunks) * kFluidCols, st, buf);
     __syncthreads();  // buffer `buf` is refilled by the issue two items on
   }
   cp_async_wait<0>();
@@ -216,10 +249,12 @@ __device__ __forceinline__ void batch_stage_phase(const BatchTables& t, unsigned
 }
 
 // nsteps (<= kPersistSteps) coupled steps of every instance from AA parity `parity`.
-// skip_cta >= 0: that CTA leaves before its first barrier (a host-made fault that the
-// bounded wait turns into LW_ETIMEOUT).
+// with_fluid = 0: the three RK3 stages of one step only (nsteps = 1), the fluid part having
+// run in a grouped launch before this one.  skip_cta >= 0: that CTA leaves before its first
+// barrier (a host-made fault that the bounded wait turns into LW_ETIMEOUT).
 __global__ void __launch_bounds__(kWT, kPersistMinB) batch_persistent_kernel(BatchTables t, int parity, int nsteps,
-                                                               long long wait_limit, int skip_cta) {
+                                                               long long wait_limit, int skip_cta,
+                                                               int with_fluid) {
   __shared__ __align__(16) unsigned char smem_buf[kPersistSmem];
   StageWideSmem& S = *reinterpret_cast<StageWideSmem*>(smem_buf);
   __shared__ Args<float> sa;
@@ -230,13 +265,16 @@ __global__ void __launch_bounds__(kWT, kPersistMinB) batch_persistent_kernel(Bat
   if (threadIdx.x == 0) s_inst = -1;
   __syncthreads();
   const unsigned nb = gridDim.x;
+  if (!with_fluid) nsteps = min(nsteps, 1);
   for (int k = 0; k < nsteps; ++k) {
-    FluidStage& fs = *reinterpret_cast<FluidStage*>(smem_buf);
-    if (((parity + k) & 1) == 0)
-      batch_fluid_phase<0>(t, fs, sa, s_inst);
-    else
-      batch_fluid_phase<1>(t, fs, sa, s_inst);
-    if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
+    if (with_fluid) {
+      FluidStage& fs = *reinterpret_cast<FluidStage*>(smem_buf);
+      if (((parity + k) & 1) == 0)
+        batch_fluid_phase<0>(t, fs, sa, s_inst);
+      else
+        batch_fluid_phase<1>(t, fs, sa, s_inst);
+      if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
+    }
     batch_stage_phase<1>(t, t.queue + 3 * k, S, sa, s_inst, s_meta);
     if (!batch_grid_sync(t, nb, wait_limit, s_ok)) return;
     batch_stage_phase<2>(t, t.queue + 3 * k + 1, S, sa, s_inst, s_meta);

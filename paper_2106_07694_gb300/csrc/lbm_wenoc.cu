@@ -948,7 +948,8 @@ struct lbm_wenoc_batch {
   int device = 0;
   int lbm_blocks = 0, st_blocks = 0;
   lw::BatchTables tab{};
-  bool persistent = true;        // one cooperative launch per graph of steps, else grouped launches
+  int mode = 1;                  // 1: one cooperative launch per graph of steps; 2: per step a grouped
+                                 // fluid launch and a cooperative stage launch; 0: grouped launches
   int grid = 0;                  // CTAs of the persistent launch (all resident at once)
   int64_t wait_limit = 1LL << 31;  // clock64 cycles a barrier wait may take (about 1 s)
   int skip_cta = -1;             // testing: this CTA leaves the next launch before its first barrier
@@ -1038,10 +1039,11 @@ int batch_upload_tables(lbm_wenoc_batch* b) {
 // four grouped launches per step.
 cudaError_t batch_enqueue(lbm_wenoc_batch* b, cudaStream_t s, int parity, int count) {
   const lw::BatchTables t = b->tab;
-  if (b->persistent) {
-    // the barrier words and the work counters start at zero; the status word is kept
+  // one cooperative launch: the barrier words and the work counters start at zero (the
+  // status word is kept)
+  auto persistent_launch = [&](int par, int steps, int with_fluid) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(t.bar, 0, sizeof(unsigned) * 2, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(t.queue, 0, sizeof(unsigned) * 3 * lw::kPersistSteps, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t.queue, 0, sizeof(unsigned) * 3 * steps, s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->grid);
@@ -1054,7 +1056,20 @@ cudaError_t batch_enqueue(lbm_wenoc_batch* b, cudaStream_t s, int parity, int co
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const long long limit = (long long)b->wait_limit;
-    return cudaLaunchKernelEx(&cfg, lw::batch_persistent_kernel, t, parity, count, limit, b->skip_cta);
+    return cudaLaunchKernelEx(&cfg, lw::batch_persistent_kernel, t, par, steps, limit, b->skip_cta, with_fluid);
+  };
+  if (b->mode == 1) return persistent_launch(parity, count, 1);
+  if (b->mode == 2) {
+    for (int k = 0; k < count; ++k) {
+      const int par = (parity + k) & 1;
+      if (par == 0)
+        lw::lbm_d2q9_batch_kernel<0><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
+      else
+        lw::lbm_d2q9_batch_kernel<1><<<b->lbm_blocks, kLbmThreads, 0, s>>>(t);
+      const cudaError_t e = persistent_launch(par, 1, 0);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
   }
   for (int k = 0; k < count; ++k) {
     const int par = (parity + k) & 1;
@@ -1085,7 +1100,9 @@ int batch_capture(lbm_wenoc_batch* b, int parity, int count, cudaGraphExec_t* ou
   return e == cudaSuccess ? LW_OK : LW_ECUDA;
 }
 
-int64_t batch_launches(const lbm_wenoc_batch* b, int count) { return b->persistent ? 1 : 4LL * count; }
+int64_t batch_launches(const lbm_wenoc_batch* b, int count) {
+  return b->mode == 1 ? 1 : (b->mode == 2 ? 2LL * count : 4LL * count);
+}
 
 // Advance every instance; requires equal step counts (shared AA parity).  Graphs of
 // kGraphSteps steps (and of one step for the rest) are captured once per parity.
@@ -1192,7 +1209,7 @@ int lbm_wenoc_batch_create(const lbm_wenoc_params* p, int32_t count, void* dev_w
     return LW_ECUDA;
   }
   b->grid = per_sm * sms;
-  b->persistent = coop != 0 && b->grid > 0;
+  b->mode = coop != 0 && b->grid > 0 ? 1 : 0;
   size_t off = 0;
   for (int i = 0; i < count; ++i) {
     const size_t sz = align_up(make_layout(p[i]).total, 256);
@@ -1231,13 +1248,13 @@ int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps) {
 }
 
 int lbm_wenoc_batch_set_persistent(lbm_wenoc_batch* b, int32_t persistent) {
-  if (!b) return LW_EINVAL;
+  if (!b || persistent < 0 || persistent > 2) return LW_EINVAL;
   int coop = 0;
   if (persistent && (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device) != cudaSuccess ||
                      !coop || b->grid <= 0))
     return LW_EINVAL;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LW_ECUDA;
-  b->persistent = persistent != 0;
+  b->mode = persistent;
   batch_destroy_graphs(b);
   return LW_OK;
 }

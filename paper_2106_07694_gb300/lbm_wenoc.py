@@ -475,7 +475,10 @@ def lbm_wenoc_batch_autotune(b, count, steps_per_trial=4):
 
 
 def lbm_wenoc_batch_set_persistent(b, persistent=True):
-    return _check("lbm_wenoc_batch_set_persistent", load().lbm_wenoc_batch_set_persistent(b, 1 if persistent else 0))
+    """True/1: one persistent launch per graph of steps; 2: grouped fluid launch + persistent
+    stage launch per step; False/0: grouped launches."""
+    mode = int(persistent) if not isinstance(persistent, bool) else (1 if persistent else 0)
+    return _check("lbm_wenoc_batch_set_persistent", load().lbm_wenoc_batch_set_persistent(b, mode))
 
 
 def lbm_wenoc_batch_set_wait_limit(b, cycles, skip_cta=-1):

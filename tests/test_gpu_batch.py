@@ -43,7 +43,7 @@ def _alone(steps):
     return out
 
 
-@pytest.mark.parametrize("persistent,tune", [(True, False), (True, True), (False, False)])
+@pytest.mark.parametrize("persistent,tune", [(1, False), (1, True), (2, False), (2, True), (0, False)])
 def test_batch_matches_instances_run_alone_bitwise(persistent, tune):
     from paper_2106_07694_gb300.lbm_wenoc import Batch
     b = Batch(SPECS)
@@ -84,13 +84,15 @@ def test_persistent_batch_of_many_instances_bitwise():
         assert inst.deposit == s.deposit
 
 
-def test_persistent_batch_barrier_wait_times_out_and_recovers():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_persistent_batch_barrier_wait_times_out_and_recovers(mode):
     # One CTA is told to leave before its first barrier; the others' bounded waits (about
     # 10 ms here) run out, the launch ends and the batch reports LW_ETIMEOUT once.  After
     # re-initialisation the batch steps normally again, bit for bit as before.
     from paper_2106_07694_gb300 import lbm_wenoc as lw
     from paper_2106_07694_gb300.lbm_wenoc import Batch
     b = Batch(SPECS)
+    b.set_persistent(mode)
     for inst, c0 in zip(b.instances, _inits()):
         inst.init(c0)
     lw.lbm_wenoc_batch_set_wait_limit(b.handle, 20_000_000, 0)
