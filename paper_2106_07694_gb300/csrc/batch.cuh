@@ -6,7 +6,7 @@
 // once advances every instance by up to kPersistSteps steps.  A step is four phases --
 // the fluid part (collide-stream), then the three RK3 stages of the transport -- over a
 // work list of (instance, tile) items; a grid barrier separates the phases.  Fluid items
-// are one row by 256 columns, one contiguous run per CTA (uniform cost); stage items are one
+// are one row by 128 columns, one contiguous run per CTA (uniform cost); stage items are one
 // four-column-kernel strip by one row segment (the segment height is the instance's own,
 // chosen by the autotuner), taken from a per-phase counter so that uneven items balance.
 // The barrier waits on a generation word with a clock64 bound: a CTA that waits longer
@@ -141,8 +141,8 @@ __device__ __forceinline__ bool batch_grid_sync(const BatchTables& t, unsigned n
   return s_ok != 0;
 }
 
-// Fluid phase of every instance: item = one row by 256 columns (fluid_rows.cuh); the two
-// window buffers overlay the stage phases' shared block.
+// Fluid phase of every instance: item = one row by kFluidCols columns (fluid_rows.cuh);
+// the window buffers overlay the stage phases' shared block.
 constexpr size_t kPersistSmem = sizeof(StageWideSmem) > sizeof(FluidStage) ? sizeof(StageWideSmem) : sizeof(FluidStage);
 
 // Instance of a run of fluid items, kept while the items stay in it: a CTA's items are
@@ -186,15 +186,20 @@ __device__ __forceinline__ void batch_fluid_phase(const BatchTables& t, FluidSta
   const int total = __ldg(t.fl_start + t.count);
   const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
   const int first = (int)blockIdx.x * per, last = min(total, first + per);
-  FluidCursor ci, cc;  // the issuing side (one item ahead) and the computing side
+  constexpr int kAhead = kFluidBufs - 1;
+  FluidCursor ci, cc;  // the issuing side (kAhead items ahead) and the computing side
   int inst = s_inst;   // the instance in sa (the same in every thread)
-  int buf = 0;
-  if (first < last) fluid_issue<PARITY>(t, ci, first, st, 0);
-  cp_async_commit();
-  for (int item = first; item < last; ++item, buf ^= 1) {
-    if (item + 1 < last) fluid_issue<PARITY>(t, ci, item + 1, st, buf ^ 1);
+#pragma unroll
+  for (int j = 0; j < kAhead; ++j) {
+    if (first + j < last) fluid_issue<PARITY>(t, ci, first + j, st, j);
     cp_async_commit();
-    cp_async_wait<1>();  // this item's windows (the next item's copies may still fly)
+  }
+  int buf = 0;
+  for (int item = first; item < last; ++item, buf = buf == kFluidBufs - 1 ? 0 : buf + 1) {
+    const int ahead = item + kAhead;
+    if (ahead < last) fluid_issue<PARITY>(t, ci, ahead, st, buf == 0 ? kFluidBufs - 1 : buf - 1);
+    cp_async_commit();
+    cp_async_wait<kAhead>();  // this item's windows (the later items' copies may still fly)
     fluid_seek(t, cc, item);
     __syncthreads();     // every thread's copies have landed; sa is no longer read
     if (cc.i != inst) {  // uniform: every thread computed the same cursor
@@ -207,7 +212,7 @@ __device__ __forceinline__ void batch_fluid_phase(const BatchTables& t, FluidSta
     }
     const int local = item - cc.start;
     fluid_compute_row<PARITY>(sa, local / cc.chunks, (local % cc.chunks) * kFluidCols, st, buf);
-    __syncthreads();  // buffer `buf` is refilled by the issue two items on
+    __syncthreads();  // buffer `buf` is refilled by the next item's issue
   }
   cp_async_wait<0>();
   __syncthreads();

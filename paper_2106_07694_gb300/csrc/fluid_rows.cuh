@@ -1,10 +1,11 @@
-// The fluid part of a coupled step (collide-stream, AA pattern) over row items of 256
-// columns, for kernels whose CTAs take such items between other work: 64 threads x 4 nodes
-// (x = x0 + t + 64 q).  The populations an item reads -- for each direction i one row
-// window of 264 columns (the item's columns and a four-column quad on each side, for the
-// x-shifted pulls of the odd AA step) -- are copied into shared memory with asynchronous
-// 16-byte copies (cp.async.cg: at L2, no L1 line), so that many bytes are in flight per SM
-// without holding registers; the collision then reads them from shared memory.
+// The fluid part of a coupled step (collide-stream, AA pattern) over row items of
+// kFluidCols columns, for kernels whose CTAs take such items between other work: 64 threads
+// x kFluidCols / 64 nodes (x = x0 + t + 64 q).  The populations an item reads -- for each
+// direction i one row window of kFluidCols + 8 columns (the item's columns and a four-column
+// quad on each side, for the x-shifted pulls of the odd AA step) -- are copied into shared
+// memory with asynchronous 16-byte copies (cp.async.cg: at L2, no L1 line), kFluidBufs - 1
+// items ahead, so that many bytes are in flight per SM without holding registers; the
+// collision then reads them from shared memory.
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
@@ -12,12 +13,14 @@
 
 namespace lw {
 
-constexpr int kFluidCols = 256;                 // columns of a fluid item (64 threads x 4 nodes)
+constexpr int kFluidCols = 128;                 // columns of a fluid item (64 threads x 2 nodes)
+constexpr int kFluidBufs = 4;                   // item buffers: one collided, the others in flight
 constexpr int kFlQuads = kFluidCols / 4 + 2;    // 16-byte quads of a population row window
 constexpr int kFluidPair = 2;                   // nodes a thread collides together
+constexpr int kFluidNodes = kFluidCols / 64;    // nodes per thread and item
 struct FluidStage {
-  float4 w[2][9][kFlQuads];      // two items' population windows (one filled while the other is used)
-  float4 c[2][kFluidCols / 4];   // and their c (the force)
+  float4 w[kFluidBufs][9][kFlQuads];     // items' population windows
+  float4 c[kFluidBufs][kFluidCols / 4];  // and their c (the force)
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -41,14 +44,14 @@ __device__ __forceinline__ int fluid_src_shift(int i, bool wall) {
 template <int PARITY>
 __device__ __forceinline__ void fluid_issue_row(const float* G, const float* C, unsigned n, int nx, int ny, int y,
                                                 int x0, FluidStage& st, int buf) {
-  // this thread's quads of every window: q = t and q = t + 64 (the last two quads)
+  // this thread's quads of every window: q = t and q = t + 64
   const int t = (int)threadIdx.x;
   int col0 = x0 - 4 + 4 * t;  // wrapped into [0, nx): quads never straddle the wrap (nx % 4 == 0)
   while (col0 < 0) col0 += nx;
   while (col0 >= nx) col0 -= nx;
   int col1 = x0 - 4 + 4 * (t + 64);
   while (col1 >= nx) col1 -= nx;
-  const bool two = t + 64 < kFlQuads;
+  const bool one = t < kFlQuads, two = t + 64 < kFlQuads;
 #pragma unroll
   for (int d = 0; d < 9; ++d) {
     int plane = d, row = y;
@@ -60,12 +63,14 @@ __device__ __forceinline__ void fluid_issue_row(const float* G, const float* C, 
       }
     }
     const float* src = G + (size_t)plane * n + (size_t)row * nx;
-    cp_async16(&st.w[buf][d][t], src + col0);
+    if (one) cp_async16(&st.w[buf][d][t], src + col0);
     if (two) cp_async16(&st.w[buf][d][t + 64], src + col1);
   }
-  int cc = x0 + 4 * t;  // this thread's quad of c
-  while (cc >= nx) cc -= nx;
-  cp_async16(&st.c[buf][t], C + (size_t)y * nx + cc);
+  if (t < kFluidCols / 4) {
+    int cc = x0 + 4 * t;  // this thread's quad of c
+    while (cc >= nx) cc -= nx;
+    cp_async16(&st.c[buf][t], C + (size_t)y * nx + cc);
+  }
 }
 
 // Collide-stream the item's nodes from the windows in buffer buf; u goes to a.u.
@@ -74,7 +79,7 @@ __device__ __forceinline__ void fluid_compute_row(const Args<float>& sa, int y, 
                                                   int buf) {
   const float* W = reinterpret_cast<const float*>(&st.w[buf][0][0]);
 #pragma unroll 1
-  for (int q0 = 0; q0 < 4; q0 += kFluidPair) {  // kFluidPair nodes interleaved
+  for (int q0 = 0; q0 < kFluidNodes; q0 += kFluidPair) {  // kFluidPair nodes interleaved
     D2Q9Node nd[kFluidPair];
     float g[kFluidPair][9];
 #pragma unroll
