@@ -71,6 +71,17 @@ __device__ __forceinline__ T settling_at(const Args<T>& a, long long m) {
   return a.S ? a.vs * (T(1) - a.ks * a.S[m]) : a.vs;
 }
 
+// Asynchronous 16-byte global -> shared copy at L2 (cp.async.cg: no L1 line, so it also
+// sees what other SMs wrote earlier in the same launch); groups of copies are committed
+// and waited for per thread.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // fused multiply-add of the kernel's precision (fmaf for FP32, fma for FP64)
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }

@@ -23,14 +23,6 @@ struct FluidStage {
   float4 c[kFluidBufs][kFluidCols / 4];  // and their c (the force)
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Column offset of direction i's source window for this parity and row (the odd step pulls
 // g_opp(i) from x - c_i, or its own g_i when x - c_i is behind a wall).
 template <int PARITY>

@@ -41,6 +41,7 @@ struct StageWideSmem {
   float4 ym[kWring][kWT];
   float fx[2][kWT + 1];  // first left x face of each thread (+ the strip's right edge), by row parity
   float edge[kWmaxH];    // the strip's right-edge x face for each row of the segment
+  float4 cn[3][kWT];     // stages 2, 3: c^n of rows k .. k+2 at each thread's columns (cp.async ring)
   double red[kWT / 32];
   bool last;
 };
@@ -156,8 +157,14 @@ __device__ __forceinline__ void stage2d_wide_body(StageWideSmem& S, const Args<f
   fetch_x(kb);
   stage_x(kb & 1);
   fetch_x(kb + 1);  // kb + 1 <= y0 < ny
-  float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (STAGE > 1) cn = LD::v4(a.c + (unsigned)kb * (unsigned)nx + X);
+  // stages 2, 3: c^n of this thread's columns, copied two rows ahead into a three-row ring
+  // (each thread reads back only its own copies: a wait per thread, no barrier)
+  auto fetch_cn = [&](int r) {
+    if (STAGE > 1 && r < y1) cp_async16(&S.cn[r % 3][t], a.c + (unsigned)r * (unsigned)nx + X);
+    if (STAGE > 1) cp_async_commit();
+  };
+  fetch_cn(kb);
+  fetch_cn(kb + 1);
   float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
   double dep = 0.0;  // stage 3, floor row: this thread's Vs-free deposit term
   __syncthreads();
@@ -227,6 +234,11 @@ __device__ __forceinline__ void stage2d_wide_body(StageWideSmem& S, const Args<f
     __syncthreads();
 
     // ---- divergence and the Shu-Osher combination of this stage
+    float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (STAGE > 1) {
+      cp_async_wait<1>();  // row k landed (row k + 1 may still fly)
+      cn = S.cn[k % 3][t];
+    }
     if (!prime) {
       const float fr[4] = {fxq[1], fxq[2], fxq[3], S.fx[b][t + 1]};
       const float ch[4] = {cq.x, cq.y, cq.z, cq.w};
@@ -261,8 +273,9 @@ __device__ __forceinline__ void stage2d_wide_body(StageWideSmem& S, const Args<f
       }
     }
     carry = make_float4(fup[0], fup[1], fup[2], fup[3]);
-    if (STAGE > 1 && k + 1 < y1) cn = LD::v4(a.c + (unsigned)(k + 1) * (unsigned)nx + X);
+    fetch_cn(k + 2);
   }
+  if (STAGE > 1) cp_async_wait<0>();
 
   // stage 3: the CTAs holding the floor row fold the deposit of this step (FP64, fixed
   // order: warp shuffles, then the last CTA sums the per-CTA partials in strip order)
