@@ -142,6 +142,20 @@ int lbm_wenoc_mass_below(lbm_wenoc* h, int32_t level, double* out);
  * be NULL; each may be host or device memory.  Synchronises. */
 int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c);
 
+/* Checkpoint and resume: the state a step reads -- populations, the current c (and S,
+ * class fields), u, the FP64 deposits, the AA parity and the step count -- as one blob
+ * with a header.  A handle with the same parameters (LW_NO_GRAPH aside) that loads it
+ * continues bit for bit as the saved one would have.
+ *   lbm_wenoc_state_bytes  blob size for this handle.
+ *   lbm_wenoc_save_state   after the steps enqueued so far; dst host or device memory of at
+ *                          least that size (LW_ENOMEM if smaller; LW_ESTATE before init).
+ *   lbm_wenoc_load_state   src host or device memory; LW_EINVAL if the header is not a
+ *                          state of a handle with these parameters.  Clears the status word.
+ * Both synchronise the stream. */
+int lbm_wenoc_state_bytes(const lbm_wenoc* h, size_t* bytes);
+int lbm_wenoc_save_state(lbm_wenoc* h, void* dst, size_t bytes);
+int lbm_wenoc_load_state(lbm_wenoc* h, const void* src, size_t bytes);
+
 /* Synchronise and return LW_OK or LW_EUNSTABLE from the device status word. */
 int lbm_wenoc_status(lbm_wenoc* h);
 

@@ -2,6 +2,7 @@
 // carve-up of the caller's workspace, kernel launches, CUDA-graph replay of whole
 // steps, FP64 read-backs and per-kernel event timing.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -217,6 +218,15 @@ const char* kKindNames[K_COUNT] = {"lbm_collide_stream", "rk_stage1",  "rk_stage
                                    "adj_gather",         "adj_gather_fluid", "sugar_upwind"};
 // The 3D FP32 stage kernels are timed under the rk_stage* names.
 
+// NVTX range over a scope (an API call, or a kernel enqueued outside graph capture), for
+// profilers that show them (nsys, ncu --nvtx); without an attached tool a push is a test.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 cudaEvent_t take_event(lbm_wenoc* h) {
   if (h->event_pool.empty()) {
     cudaEvent_t e;
@@ -244,6 +254,7 @@ void fold_pending(lbm_wenoc* h) {
 // Wrap one launch: optional event pair, launch counting.
 template <typename F>
 void launch(lbm_wenoc* h, int kind, F&& f) {
+  NvtxRange range(kKindNames[kind]);
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (h->profiling) {
     if (h->pending.size() >= 4096) {
@@ -611,6 +622,7 @@ int lbm_wenoc_create(const lbm_wenoc_params* p, void* dev_workspace, size_t byte
 }
 
 int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
+  NvtxRange range("lbm_wenoc_init");
   if (!h || !c0) return LW_EINVAL;
   h->cur = 0;
   const size_t es = h->fp64 ? 8 : 4;
@@ -659,6 +671,7 @@ int lbm_wenoc_init(lbm_wenoc* h, const void* c0, const void* u0) {
 }
 
 int lbm_wenoc_step(lbm_wenoc* h, int64_t nsteps) {
+  NvtxRange range("lbm_wenoc_step");
   if (!h || nsteps < 0) return LW_EINVAL;
   if (!h->initialised) return LW_ESTATE;
   int64_t left = nsteps;
@@ -762,6 +775,7 @@ int lbm_wenoc_mass_below(lbm_wenoc* h, int32_t level, double* out) {
 }
 
 int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
+  NvtxRange range("lbm_wenoc_fields");
   if (!h) return LW_EINVAL;
   if (!h->initialised) return LW_ESTATE;
   const size_t es = h->fp64 ? 8 : 4;
@@ -802,6 +816,116 @@ int lbm_wenoc_fields(lbm_wenoc* h, void* rho, void* u, void* c) {
   const size_t c_off = h->ncls > 1 ? h->L.ctot : (h->sweep && h->cur ? h->L.c1 : h->L.c);
   if (c && !copy_out(c, h->ws + c_off, cbytes)) return LW_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  return LW_OK;
+}
+
+// ---- resumable state: a header, then the fields a step reads (populations, the current c,
+// u, the current S, the class fields) and the FP64 deposit scalars
+namespace {
+
+constexpr uint32_t kStateMagic = 0x5453574cu;  // "LWST"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+  uint32_t magic, version;
+  lbm_wenoc_params p;
+  int32_t parity, cur;
+  int64_t steps;
+  uint64_t bytes;
+};
+
+struct StateRegion {
+  size_t off, bytes;  // in the workspace
+};
+
+std::vector<StateRegion> state_regions(const lbm_wenoc* h) {
+  const size_t es = h->fp64 ? 8 : 4, n = (size_t)h->n;
+  const Layout& L = h->L;
+  std::vector<StateRegion> r;
+  r.push_back({L.g, (size_t)(h->p.dim == 2 ? 9 : 19) * n * es});
+  r.push_back({h->sweep && h->cur ? L.c1 : L.c, n * es});
+  r.push_back({L.u, (size_t)h->p.dim * n * es});  // read by a frozen-velocity step
+  if (h->sugar) r.push_back({h->cur ? L.sb : L.sa, n * es});
+  if (h->ncls > 1) r.push_back({L.cls, L.ctot + n * es - L.cls});
+  r.push_back({L.scalars, sizeof(double) * kScalars});
+  return r;
+}
+
+// the same simulation (field by field: the struct has padding); LW_NO_GRAPH only changes
+// how steps are launched
+bool same_params(const lbm_wenoc_params& a, const lbm_wenoc_params& b) {
+  bool eq = a.dim == b.dim && a.nx == b.nx && a.ny == b.ny && (a.dim == 2 || a.nz == b.nz) && a.tau == b.tau &&
+            a.gravity == b.gravity && a.density_contrast == b.density_contrast &&
+            a.settling_velocity == b.settling_velocity && a.diffusivity == b.diffusivity &&
+            a.lf_alpha == b.lf_alpha && a.u_cap == b.u_cap && (a.flags | LW_NO_GRAPH) == (b.flags | LW_NO_GRAPH) &&
+            a.sugar_contrast == b.sugar_contrast && a.sugar_diffusivity == b.sugar_diffusivity && a.phi0 == b.phi0 &&
+            a.vs_sugar == b.vs_sugar && a.n_classes == b.n_classes;
+  for (int d = 0; d < 3; ++d) eq = eq && a.body_force[d] == b.body_force[d];
+  for (int k = 0; k < 8; ++k) eq = eq && a.class_vs[k] == b.class_vs[k];
+  return eq;
+}
+
+size_t state_bytes(const lbm_wenoc* h) {
+  size_t b = align_up(sizeof(StateHeader), 256);
+  for (const StateRegion& r : state_regions(h)) b += align_up(r.bytes, 256);
+  return b;
+}
+
+}  // namespace
+
+int lbm_wenoc_state_bytes(const lbm_wenoc* h, size_t* bytes) {
+  if (!h || !bytes) return LW_EINVAL;
+  *bytes = state_bytes(h);
+  return LW_OK;
+}
+
+int lbm_wenoc_save_state(lbm_wenoc* h, void* dst, size_t bytes) {
+  if (!h || !dst) return LW_EINVAL;
+  if (!h->initialised) return LW_ESTATE;
+  const size_t need = state_bytes(h);
+  if (bytes < need) return LW_ENOMEM;
+  StateHeader hd{};
+  hd.magic = kStateMagic;
+  hd.version = kStateVersion;
+  hd.p = h->p;
+  hd.parity = h->parity;
+  hd.cur = h->cur;
+  hd.steps = h->steps;
+  hd.bytes = need;
+  unsigned char* d = static_cast<unsigned char*>(dst);
+  if (cudaMemcpyAsync(d, &hd, sizeof(hd), cudaMemcpyDefault, h->stream) != cudaSuccess) return LW_ECUDA;
+  size_t off = align_up(sizeof(StateHeader), 256);
+  for (const StateRegion& r : state_regions(h)) {
+    if (cudaMemcpyAsync(d + off, h->ws + r.off, r.bytes, cudaMemcpyDefault, h->stream) != cudaSuccess)
+      return LW_ECUDA;
+    off += align_up(r.bytes, 256);
+  }
+  // the header lives on this stack frame and dst may be pageable host memory
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? LW_OK : LW_ECUDA;
+}
+
+int lbm_wenoc_load_state(lbm_wenoc* h, const void* src, size_t bytes) {
+  if (!h || !src || bytes < sizeof(StateHeader)) return LW_EINVAL;
+  StateHeader hd{};
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaMemcpy(&hd, src, sizeof(hd), cudaMemcpyDefault) != cudaSuccess) return LW_ECUDA;
+  if (hd.magic != kStateMagic || hd.version != kStateVersion || !same_params(hd.p, h->p) ||
+      hd.parity < 0 || hd.parity > 1 || hd.cur < 0 || hd.cur > 1 || hd.steps < 0)
+    return LW_EINVAL;
+  h->cur = hd.cur;  // selects the buffers the regions go to
+  if (hd.bytes != state_bytes(h) || bytes < hd.bytes) return LW_EINVAL;
+  const unsigned char* sp = static_cast<const unsigned char*>(src);
+  size_t off = align_up(sizeof(StateHeader), 256);
+  for (const StateRegion& r : state_regions(h)) {
+    if (cudaMemcpyAsync(h->ws + r.off, sp + off, r.bytes, cudaMemcpyDefault, h->stream) != cudaSuccess)
+      return LW_ECUDA;
+    off += align_up(r.bytes, 256);
+  }
+  if (cudaMemsetAsync(h->ws + h->L.status, 0, sizeof(unsigned) * 4, h->stream) != cudaSuccess) return LW_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LW_ECUDA;
+  h->parity = hd.parity;
+  h->steps = hd.steps;
+  h->initialised = true;
   return LW_OK;
 }
 
@@ -1243,6 +1367,7 @@ lbm_wenoc* lbm_wenoc_batch_instance(lbm_wenoc_batch* b, int32_t i) {
 }
 
 int lbm_wenoc_batch_step(lbm_wenoc_batch* b, int64_t nsteps) {
+  NvtxRange range("lbm_wenoc_batch_step");
   if (!b) return LW_EINVAL;
   return batch_advance(b, nsteps, true);
 }
@@ -1679,6 +1804,7 @@ int lbm_wenoc_gradient_workspace_bytes(const lbm_wenoc_params* p, int64_t nsteps
 
 int lbm_wenoc_deposit_gradient(lbm_wenoc* h, const void* c0, int64_t nsteps, int32_t segment, void* adj_workspace,
                                size_t bytes, void* grad_c0, double* dJ_dVs, double* J) {
+  NvtxRange range("lbm_wenoc_deposit_gradient");
   if (!h || !c0 || !grad_c0 || !dJ_dVs || !J || nsteps < 1 || segment < 1 || !adj_workspace) return LW_EINVAL;
   if (!gradient_params_ok(h)) return LW_EINVAL;
   if (24.0 * (double)h->n >= 2147483647.0) return LW_EINVAL;  // 32-bit offsets of the face records

@@ -46,6 +46,7 @@ EXPORTED = [
     "lbm_wenoc_batch_set_wait_limit", "lbm_wenoc_batch_status",
     "lbm_wenoc_gradient_workspace_bytes", "lbm_wenoc_deposit_gradient", "lbm_wenoc_set_sugar",
     "lbm_wenoc_sugar", "lbm_wenoc_set_class", "lbm_wenoc_class", "lbm_wenoc_class_deposit",
+    "lbm_wenoc_state_bytes", "lbm_wenoc_save_state", "lbm_wenoc_load_state",
 ]
 
 
@@ -110,6 +111,9 @@ def load():
     L.lbm_wenoc_mass_below.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     L.lbm_wenoc_fields.argtypes = [vp, vp, vp, vp]
     L.lbm_wenoc_status.argtypes = [vp]
+    L.lbm_wenoc_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm_wenoc_save_state.argtypes = [vp, vp, ctypes.c_size_t]
+    L.lbm_wenoc_load_state.argtypes = [vp, vp, ctypes.c_size_t]
     L.lbm_wenoc_steps.argtypes = [vp]
     L.lbm_wenoc_steps.restype = i64
     L.lbm_wenoc_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -214,6 +218,20 @@ def lbm_wenoc_fields(h, rho=None, u=None, c=None):
 
 def lbm_wenoc_status(h):
     return load().lbm_wenoc_status(h)
+
+
+def lbm_wenoc_state_bytes(h):
+    out = ctypes.c_size_t()
+    _check("lbm_wenoc_state_bytes", load().lbm_wenoc_state_bytes(h, ctypes.byref(out)))
+    return out.value
+
+
+def lbm_wenoc_save_state(h, dst, nbytes):
+    return _check("lbm_wenoc_save_state", load().lbm_wenoc_save_state(h, _ptr(dst), int(nbytes)))
+
+
+def lbm_wenoc_load_state(h, src, nbytes):
+    return _check("lbm_wenoc_load_state", load().lbm_wenoc_load_state(h, _ptr(src), int(nbytes)))
 
 
 def lbm_wenoc_steps(h):
@@ -401,6 +419,18 @@ class Simulation:
 
     def status(self):
         return lbm_wenoc_status(self.handle)
+
+    def save_state(self, device="cuda"):
+        """The handle's resumable state as a uint8 tensor (on `device`)."""
+        import torch
+        nbytes = lbm_wenoc_state_bytes(self.handle)
+        out = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        lbm_wenoc_save_state(self.handle, out, nbytes)
+        return out
+
+    def load_state(self, state):
+        """Continue from a state saved by a handle with the same parameters."""
+        lbm_wenoc_load_state(self.handle, state, state.numel())
 
     def set_sugar(self, S0):
         """Sugar field of a sugar=True handle (after init)."""
