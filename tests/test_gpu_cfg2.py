@@ -8,8 +8,13 @@ LW_CFG2_FULL_GRID=1).
 Every 100 steps both runs give the lowest front height h_min(t) (the lowest node with
 c = 1/2 over all columns, Sec. 4.1), the deposited mass m_b(t) (Sec. 4.2) and the relative
 L2 distance of c.  Asserted:
-  * finger velocity, the least-squares slope of h_min(t) over the second half of the
-    compared span: within 2 %;
+  * finger velocity, the least-squares slope of h_min(t) over the finger phase -- from the
+    first sample where the dominant front mode exceeds 1 % of its wavelength to the deepest
+    point of the FP64 h_min after it -- within 2 %.  After that point the fingers have mixed:
+    their tips dilute below c = 1/2 and the c = 1/2 front rises again (A = 5e-5 on the full
+    lattice: 2932.7 at step 11000, 2963 at 13000), and the lowest front of the chaotic flow
+    differs between the precisions by 8-30 %, so it is no longer a finger velocity.  A run that
+    stays linear (A = 1e-5) compares the drift of the front over the second half instead;
   * m_b(t) within 2 % of the curve's range at every sample;
   * both runs leave the model's velocity range (|u| > u_cap = 0.1, LW_EUNSTABLE) in the
     same 100-step window, or neither does; the comparison ends at the last sample before
@@ -119,18 +124,30 @@ def _check(shape, A, vs):
     # the device front heights are lsa.front_height's
     c = r["last_c64"]
     assert np.allclose(front_heights(torch.from_numpy(c)).numpy(), lsa.front_height(c), rtol=0, atol=1e-9)
-    # finger velocity: slope of the lowest front over the second half of the span
-    sel = t > t[-1] / 2
+    # finger velocity: slope of the lowest front over the finger phase -- from the first sample
+    # where the dominant mode exceeds 1 % of its wavelength to the deepest point of the FP64
+    # lowest front after it (once the fingers mix, their tips dilute below c = 1/2 and the
+    # c = 1/2 front stops tracking them); a run that stays linear compares the drift of the
+    # front over the second half of the span instead
+    grow = np.nonzero(r["psd"] >= 1e-2)[0]
+    if grow.size:
+        i0 = int(grow[0])
+        i1 = i0 + int(np.argmin(r["h64"][i0:]))
+        assert i1 - i0 + 1 >= 10, "the finger phase is shorter than 1000 steps"
+        sel = slice(i0, i1 + 1)
+    else:
+        sel = t > t[-1] / 2
     v32 = np.polyfit(t[sel], r["h32"][sel], 1)[0]
     v64 = np.polyfit(t[sel], r["h64"][sel], 1)[0]
     assert v64 < 0 and abs(v32 - v64) <= 0.02 * abs(v64), (v32, v64)
+    window = (int(t[sel][0]), int(t[sel][-1]))
     # deposited mass curve
     span = r["m64"].max() - r["m64"].min()
     assert span > 0 and np.abs(r["m32"] - r["m64"]).max() <= 0.02 * span
     # element-wise while the front is linear
     lin = r["psd"] < 1e-2
     assert lin[0] and np.all(r["rel"][lin] <= 2e-4), r["rel"][lin].max()
-    print(f"A={A} Vs={vs} {shape}: span {t[-1]} steps, finger velocity {v32:.4e} / {v64:.4e}, "
+    print(f"A={A} Vs={vs} {shape}: span {t[-1]} steps, finger velocity {v32:.4e} / {v64:.4e} over {window}, "
           f"m_b max diff {np.abs(r['m32'] - r['m64']).max():.2e} of {span:.3e}, "
           f"c rel L2 {r['rel'][lin].max():.2e} (linear) {r['rel'].max():.2e} (all), mode {r['psd'].max():.3f}")
 
