@@ -173,18 +173,18 @@ _STAGE_SRC = ("transport_stage2d_wide.cuh", "transport_stage2d.cuh", "transport_
 _STAGE3D_SRC = ("transport_sweep3d_wide.cuh", "transport_sweep3d.cuh") + _STAGE_SRC
 NCU_TRAFFIC = {
     "lbm_collide_stream": (643.1e6, _LBM_SRC, "2097009c2aa4"),
-    "rk_stage1": (134.3e6, _STAGE_SRC, "cad59013ac22"),
-    "rk_stage2": (178.4e6, _STAGE_SRC, "cad59013ac22"),
-    "rk_stage3": (171.9e6, _STAGE_SRC, "cad59013ac22"),
+    "rk_stage1": (134.3e6, _STAGE_SRC, "dd1ee704fac2"),
+    "rk_stage2": (178.4e6, _STAGE_SRC, "dd1ee704fac2"),
+    "rk_stage3": (171.9e6, _STAGE_SRC, "dd1ee704fac2"),
     # 512 x 1024 adjoint workload (the face records stay in L2)
     "adj_faces": (8.57e6, ("adjoint.cuh",) + _LBM_SRC, "d60661f5666e"),
 }
 # the 256 x 256 x 512 D3Q19 workload
 NCU_TRAFFIC_3D = {
     "lbm_collide_stream": (5577.75e6, _LBM_SRC, "2097009c2aa4"),
-    "rk_stage1": (966.4e6, _STAGE3D_SRC, "82eaf992674e"),
-    "rk_stage2": (1127.2e6, _STAGE3D_SRC, "82eaf992674e"),
-    "rk_stage3": (1109.2e6, _STAGE3D_SRC, "82eaf992674e"),
+    "rk_stage1": (966.4e6, _STAGE3D_SRC, "5a04479acddc"),
+    "rk_stage2": (1127.2e6, _STAGE3D_SRC, "5a04479acddc"),
+    "rk_stage3": (1109.2e6, _STAGE3D_SRC, "5a04479acddc"),
 }
 
 

@@ -15,7 +15,9 @@
 //    whole segment before the sweep;
 //  - the upper y face of each of its columns comes from a private ring of the y-split
 //    fluxes of rows k-2 .. k+3 (one float4 per row and split half), filled three rows
-//    ahead; the lower y face is carried from the previous row.
+//    ahead; the lower y face is carried from the previous row;
+//  - stages 2 and 3 also combine with c^n at the node, copied two rows ahead by cp.async
+//    into a three-row ring in shared memory (no registers held while it is in flight).
 // Every face is computed once, with the arithmetic of weno5_face_value/face_flux_x, so
 // the faces and the updated c are bitwise those of the one-column kernel.
 #pragma once
