@@ -52,3 +52,14 @@ def test_traffic_is_reported_only_for_unchanged_sources(monkeypatch):
     monkeypatch.setitem(bench.NCU_TRAFFIC, name, (nbytes, ("no_such_file.cuh",), sha))
     assert bench.kernel_traffic(name) is None
     assert bench.kernel_traffic("not_a_kernel") is None
+
+
+def test_traffic_of_the_3d_workload_comes_from_its_own_table(monkeypatch):
+    name = "rk_stage1"
+    nb2, files2, _ = bench.NCU_TRAFFIC[name]
+    nb3, files3, _ = bench.NCU_TRAFFIC_3D[name]
+    assert nb3 != nb2 and files3[0].startswith("transport_sweep3d")
+    monkeypatch.setitem(bench.NCU_TRAFFIC_3D, name, (nb3, files3, bench.source_hash(files3)))
+    assert bench.kernel_traffic(name, bench.NCU_TRAFFIC_3D) == nb3
+    monkeypatch.setitem(bench.NCU_TRAFFIC_3D, name, (nb3, files3, "f" * 12))
+    assert bench.kernel_traffic(name, bench.NCU_TRAFFIC_3D) is None
