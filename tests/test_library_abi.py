@@ -93,3 +93,12 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(lw, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         lw.load()
+
+
+def test_state_and_batch_calls_reject_null_handles(lib):
+    out = ctypes.c_size_t()
+    assert lib.lbm_wenoc_state_bytes(None, ctypes.byref(out)) == lw.LW_EINVAL
+    assert lib.lbm_wenoc_save_state(None, ctypes.c_void_p(4096), ctypes.c_size_t(1 << 20)) == lw.LW_EINVAL
+    assert lib.lbm_wenoc_load_state(None, ctypes.c_void_p(4096), ctypes.c_size_t(1 << 20)) == lw.LW_EINVAL
+    for mode in (0, 1, 2, 3, -1):
+        assert lib.lbm_wenoc_batch_set_persistent(None, mode) == lw.LW_EINVAL
