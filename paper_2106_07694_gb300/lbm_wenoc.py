@@ -429,8 +429,10 @@ class Simulation:
         return out
 
     def load_state(self, state):
-        """Continue from a state saved by a handle with the same parameters."""
-        lbm_wenoc_load_state(self.handle, state, state.numel())
+        """Continue from a state saved by a handle with the same parameters (a uint8 tensor
+        from save_state, on any device, or a numpy byte array)."""
+        nbytes = state.nbytes if isinstance(state, np.ndarray) else state.numel() * state.element_size()
+        lbm_wenoc_load_state(self.handle, state, nbytes)
 
     def set_sugar(self, S0):
         """Sugar field of a sugar=True handle (after init)."""
